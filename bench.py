@@ -1,0 +1,307 @@
+"""Benchmark of the GB300 triad census (one JSON line on rank 0).
+
+A step is one full census (Fig. 5) of the scale-20 R-MAT workload: n = 2^20, edge factor
+16, a/b/c/d = .57/.19/.19/.05, ids permuted, loops and duplicates dropped, 20% of arcs
+reciprocated, seed 2.  `value` is arcs/s with the CSR resident in HBM (device time per
+census from CUDA events on the launching stream, L2 flushed by a 512 MB write between
+steps, outside the events).  `e2e` is the same metric through the public C ABI from pinned
+host arc buffers: graph build (H2D copy, symmetrise, dedupe, relabel, sort) plus census plus
+the D2H read of the 16 counts, every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--algo suffix|union] [--impl reference]
+
+--impl reference times the CPU oracle (test infrastructure, single-threaded) on a bounded
+sample of the same workload.  Under torchrun (N > 1) every rank runs the same census on its
+own GPU (replicas, weak scaling); only the barrier and the max-over-ranks time cross ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "triad-census arcs/sec (bit-exact), learned/batched vs plain; % HBM roofline"
+WORKLOAD = dict(name="rmat20_ef16_r20_seed2", scale=20, edge_factor=16, recip=0.2, seed=2)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_census_rmat20_traffic.txt")
+CENSUS_SRC = os.path.join(ROOT, "paper_1209_6308_gb300", "csrc", "census.cu")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--algo", default="suffix", choices=["suffix", "union"])
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-stride", type=int, default=0)
+    return p.parse_args()
+
+
+def workload():
+    import graphgen
+    return graphgen.rmat(WORKLOAD["scale"], WORKLOAD["edge_factor"], WORKLOAD["recip"], WORKLOAD["seed"])
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"tc_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+CPU_STRIDE = 256          # cpu_baseline: ~0.2% of the union-walk work, ~30 s on one core
+REF_STRIDE = 4096         # reference arm: per-step sample, a few seconds each
+
+
+def oracle_sample(og, stride, offset):
+    """Fig. 5 loop of the CPU oracle over vertices u = offset (mod stride); returns
+    (estimated seconds for the full census, sample seconds, work fraction)."""
+    sec, _, ws, wt = og.sample(stride, offset)
+    frac = ws / wt if wt else 1.0
+    return (sec / frac if frac > 0 else float("inf")), sec, frac
+
+
+def cpu_baseline(n, s, d, arcs, stride):
+    import oracle
+    og = oracle.SampledGraph(n, s, d)
+    full, sec, frac = oracle_sample(og, stride, 0)
+    og.close()
+    return {"value": arcs / full, "unit": "arcs/s", "cores": 1, "kind": "oracle",
+            "sample": (f"single-threaded Fig. 5 oracle over vertices u = 0 (mod {stride}) of the same graph: "
+                       f"{sec:.1f} s for {frac * 100:.3f}% of the union-walk work, scaled to the full census")}
+
+
+def run_reference(args):
+    import oracle
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    n, s, d = workload()
+    arcs = len(s)
+    stride = args.cpu_sample_stride or REF_STRIDE
+    og = oracle.SampledGraph(n, s, d)
+    times, secs, fracs = [], [], []
+    for i in range(args.warmup + args.steps):
+        full, sec, frac = oracle_sample(og, stride, i % stride)
+        if i >= args.warmup:
+            times.append(full)
+            secs.append(sec)
+            fracs.append(frac)
+    og.close()
+    t = sum(secs) / sum(fracs)         # pooled estimate of the full-census time
+    v = arcs / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "arcs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "n": n, "arcs": arcs},
+            "cpu_baseline": {"value": v, "unit": "arcs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"step i: Fig. 5 loop over u = i (mod {stride}); full-census time "
+                                       f"estimated as total sample seconds / total work fraction "
+                                       f"({sum(fracs) * 100:.3f}% of the union-walk work)"},
+            "e2e": {"value": v, "unit": "arcs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def stored_traffic():
+    """Per-launch DRAM bytes from the committed ncu summary, if taken on this census.cu."""
+    try:
+        kv = dict(line.split(":", 1) for line in open(TRAFFIC_FILE) if ":" in line)
+        src_hash = hashlib.sha256(open(CENSUS_SRC, "rb").read()).hexdigest()[:16]
+        if kv.get("census_cu_sha256_16", "").strip() == src_hash:
+            return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def run_gpu(args):
+    import torch
+    import paper_1209_6308_gb300 as tc
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    algo = tc.TC_ALGO_SUFFIX if args.algo == "suffix" else tc.TC_ALGO_UNION
+    opts = {"algo": algo}
+    n, s, d = workload()
+    arcs = len(s)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+
+    g = tc.Graph.from_arcs(n, s, d, stream=sh, options=opts)
+    info = g.stats()
+    opts_run = opts
+    out = torch.zeros(16, dtype=torch.int64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_census():
+        tc.tc_census_async(g.handle, out, stream=sh, options=opts_run)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            one_census()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.zero_()
+                starts[i].record(stream)
+                one_census()
+                ends[i].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    counts = [int(x) & ((1 << 64) - 1) for x in out.cpu().tolist()]
+    counts[0] = tc.tc_null_count(n, counts)
+
+    # end to end through the C ABI from pinned host buffers
+    src_pin = torch.from_numpy(s.view("int32")).pin_memory()
+    dst_pin = torch.from_numpy(d.view("int32")).pin_memory()
+    e2e_ms = []
+    e2e_counts = None
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = tc.tc_graph_create_arcs(n, src_pin, dst_pin, stream=sh, options=opts)
+        c = tc.tc_census(h, stream=sh, options=opts_run)
+        tc.tc_graph_destroy(h)
+        dt = (time.perf_counter() - t0) * 1e3
+        if i:
+            e2e_ms.append(dt)
+        e2e_counts = c
+    g.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = measured_peak()
+    bytes_alg = info["bytes_alg"]
+    achieved = bytes_alg / (ms * 1e-3) / 1e9
+    traffic = stored_traffic()
+    line = {
+        "metric": METRIC, "value": world * arcs / (ms * 1e-3),
+        "unit": "arcs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "n": n, "arcs": arcs, "e_sym": info["e_sym"],
+                   "algo": args.algo, "schedule": "plain", "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "k_census", "bytes_alg_per_launch": bytes_alg},
+        "e2e": ({"value": world * arcs / (statistics.mean(e2e_ms) * 1e-3), "unit": "arcs/s",
+                 "h2d_bytes_per_step": 8 * arcs, "d2h_bytes_per_step": 16 * 16,
+                 "ms_per_step": statistics.mean(e2e_ms)} if e2e_ms else None),
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "census": counts,
+        "census_e2e_equal": (e2e_counts == counts) if e2e_counts else None,
+        "step_ms": {"min": min(step_ms), "max": max(step_ms)},
+        "timed_wall_s": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n, s, d, arcs, args.cpu_sample_stride or CPU_STRIDE)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,151 @@
+/*
+ * tc.h - C ABI of the GB300 triad-census library (libtc.so).
+ *
+ * Computes the exact 16-type directed triad census of Batagelj and Mrvar (paper Sec. 4,
+ * Fig. 5) on one GPU.  The graph is held as the compact structure of Sec. 6 (Fig. 7): one
+ * edge array, a start offset per vertex, and the neighbour id stored with two low direction
+ * bits.  All signatures use plain C types and pointers; nothing here depends on PyTorch.
+ *
+ * Census index order (0-based), used by every output array:
+ *   0 003   1 012   2 102   3 021D  4 021U  5 021C  6 111D  7 111U
+ *   8 030T  9 030C 10 201  11 120D 12 120U 13 120C 14 210  15 300
+ * (Fig. 5 step 5 fixes index 0 = null triads, step 2.1.2 fixes 1 = one asymmetric dyad and
+ * 2 = one mutual dyad; the others follow the usual mutual-asymmetric-null order.)
+ *
+ * Conventions for every entry point:
+ *   - Return a tc_status; TC_OK is 0.  On failure nothing is written to the outputs, and
+ *     tc_last_error() returns a message for the calling thread.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Device memory the library needs for a graph is allocated stream-ordered on the
+ *     graph's creation stream and owned by the tc_graph until tc_graph_destroy.
+ *   - The caller keeps ownership of every buffer it passes; inputs are copied.
+ *   - Vertex ids are uint32 and must be < n; n must be <= 2^30 because each stored id
+ *     carries two direction bits (Sec. 6).
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_graph tc_graph;                 /* opaque; owns its device CSR */
+typedef struct { uint64_t lo, hi; } tc_u128;      /* unsigned 128-bit count, little-endian halves */
+
+typedef enum {
+    TC_OK = 0,
+    TC_ERR_ARG = 1,       /* null pointer, malformed CSR, bad option */
+    TC_ERR_RANGE = 2,     /* a vertex id >= n, n > 2^30, or a count beyond a documented limit */
+    TC_ERR_OOM = 3,       /* device (or pinned host) allocation failed */
+    TC_ERR_CUDA = 4,      /* a CUDA runtime call or kernel launch failed */
+    TC_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    TC_ERR_BUSY = 6       /* the object is in use by another call */
+} tc_status;
+
+/* Which census kernel family runs the hot loop (step 2.1.4 of Fig. 5). */
+typedef enum {
+    /* Visit every third vertex w of S = N[u] u N[v] \ {u,v} and classify it through the
+     * 64-entry tricode table (Fig. 5 with the two-list walk of Sec. 6, Fig. 8). */
+    TC_ALGO_UNION = 0,
+    /* Same census; the w that only u reaches and that lie past v are classified in bulk
+     * from per-list direction-class counts instead of one by one (only dir(u,v) and
+     * dir(u,w) decide their class), so each pair costs O(|N[v]|). */
+    TC_ALGO_SUFFIX = 1
+} tc_algo;
+
+/* How the connected pairs (u,v) are grouped into GPU work items. */
+typedef enum {
+    TC_SCHED_PLAIN = 0,    /* degree-threshold tiers, cost estimated from degrees */
+    TC_SCHED_LEARNED = 1   /* tiers and hub splits from the learned per-vertex cost model */
+} tc_schedule;
+
+/* Options; zero-initialise and set what you need (0 selects the default). */
+typedef struct {
+    uint32_t algo;            /* tc_algo, default TC_ALGO_UNION */
+    uint32_t schedule;        /* tc_schedule, default TC_SCHED_PLAIN */
+    uint32_t warp_max_deg;    /* vertices u with deg <= this run one warp per u (default 64) */
+    uint32_t chunk_entries;   /* neighbour entries of u staged per CTA (default 4096, power of 2) */
+    uint32_t item_work;       /* target work per CTA item, in list entries touched (default 2^18) */
+    uint32_t ctas_per_sm;     /* persistent CTAs per SM (default 3) */
+    uint32_t reserved[10];
+} tc_options;
+
+/* Statistics of a built graph (all counts after cleaning). */
+typedef struct {
+    uint32_t n;               /* vertices, isolated ones included */
+    uint32_t max_deg;         /* largest symmetric degree */
+    uint64_t arcs;            /* distinct directed arcs; a mutual pair counts 2 */
+    uint64_t e_sym;           /* connected (unordered) pairs = upper pairs u<v */
+    uint64_t mutual;          /* mutual pairs */
+    uint64_t loops_dropped;   /* self-loops in the input */
+    uint64_t dups_dropped;    /* repeated arcs in the input */
+    uint64_t sum_d2;          /* sum over vertices of deg^2 = merge steps of the full union walk */
+    uint64_t sum_dv_upper;    /* sum over upper pairs u<v of deg(v) */
+    uint64_t bytes_alg;       /* algorithmic bytes of one census: 8(n+1) + 8 e_sym + sum(4 deg(v) + 16) + 128 */
+} tc_graph_info;
+
+/* Build a graph from an arc list (Sec. 6, Fig. 7).  src[i] -> dst[i] for i < m; self-loops
+ * and repeated arcs are dropped and counted.  Ids >= n give TC_ERR_RANGE.  src/dst are
+ * device pointers if ptr_is_device, else host pointers (copied to the device on `stream`).
+ * Vertices are relabelled by descending symmetric degree (ties by original id); the census
+ * does not depend on labels.  opt may be NULL.  The call synchronises `stream`. */
+tc_status tc_graph_create_arcs(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
+                               int ptr_is_device, void* stream, const tc_options* opt, tc_graph** out);
+
+/* Build a graph from a CSR already in the Fig. 7 form: off[n+1] (uint64) and
+ * adj_flagged[off[n]] where each entry is (id << 2) | dir, dir 1 = owner->id, 2 = id->owner,
+ * 3 = both.  Every list must be strictly ascending by id, loop-free, with dir != 0, and the
+ * lists must be symmetric (x in N[y] iff y in N[x], with mirrored dir bits); otherwise
+ * TC_ERR_ARG.  Pointers are device or host as for tc_graph_create_arcs. */
+tc_status tc_graph_create_csr(uint32_t n, const uint64_t* off, const uint32_t* adj_flagged,
+                              int ptr_is_device, void* stream, const tc_options* opt, tc_graph** out);
+
+/* Full census (Fig. 5): 16 counts, the null count (index 0) computed as C(n,3) minus the
+ * rest in 128-bit (steps 3-5).  Enqueues the kernels on `stream` and synchronises it. */
+tc_status tc_census(tc_graph* g, void* stream, tc_u128 out[16]);
+
+/* Same census with options overriding the graph's creation options (algo, schedule,
+ * tiers) for this call only.  opt may be NULL. */
+tc_status tc_census_opts(tc_graph* g, void* stream, const tc_options* opt, tc_u128 out[16]);
+
+/* Asynchronous census: enqueues the kernels on `stream` and writes, when they finish,
+ * counts of classes 1..15 to d_out16[1..15] (device memory, uint64) and 0 to d_out16[0].
+ * The null count needs 128-bit arithmetic: obtain it with tc_null_count.  Does not
+ * synchronise; d_out16 must stay valid until the stream reaches the end of the census. */
+tc_status tc_census_async(tc_graph* g, void* stream, const tc_options* opt, uint64_t* d_out16);
+
+/* Null count C(n,3) - sum(counts[1..15]) in 128-bit (Fig. 5 steps 3-5), on the host. */
+tc_u128 tc_null_count(uint32_t n, const uint64_t counts16[16]);
+
+/* Census of k graphs in one persistent launch.  out16xk receives 16 uint64 per graph
+ * (index 0 set to the low 64 bits of the null count); out003_k (may be NULL) receives each
+ * full 128-bit null count.  Host pointers.  Synchronises `stream`. */
+tc_status tc_census_batch(tc_graph* const* gs, uint32_t k, void* stream, uint64_t* out16xk,
+                          tc_u128* out003_k);
+
+tc_status tc_graph_stats(const tc_graph* g, tc_graph_info* info);
+
+/* Device pointers of the built CSR in the relabelled ids, and the relabelling:
+ * new_of_old[old id] = new id.  Valid until tc_graph_destroy.  Any out pointer may be NULL. */
+tc_status tc_graph_device_csr(const tc_graph* g, const uint64_t** off, const uint32_t** adj,
+                              const uint32_t** new_of_old);
+
+/* Copy the built CSR (relabelled ids, Fig. 7 layout) and the relabelling to host memory:
+ * off_host[n+1], adj_host[2*e_sym], new_of_old_host[n].  Any pointer may be NULL to skip
+ * that array.  Synchronous (uses the legacy default stream). */
+tc_status tc_graph_export_csr(const tc_graph* g, uint64_t* off_host, uint32_t* adj_host, uint32_t* new_of_old_host);
+
+void tc_graph_destroy(tc_graph* g);
+const char* tc_status_str(tc_status s);
+const char* tc_last_error(void);
+
+/* The 64-entry tricode -> class table the kernels use (for inspection and tests). */
+void tc_tricode_table(uint8_t out[64]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_H */

@@ -52,9 +52,11 @@ def _load():
         lib.or_census_bm_parallel.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p, ctypes.c_int]
         lib.or_census_brute.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p]
         lib.or_invariants.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p]
+        lib.or_graph_new.restype = ctypes.c_void_p
+        lib.or_graph_new.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p]
+        lib.or_graph_free.argtypes = [ctypes.c_void_p]
         lib.or_census_bm_sample.restype = ctypes.c_double
-        lib.or_census_bm_sample.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, ctypes.c_uint32,
-                                            ctypes.c_uint32, u64p, u64p, u64p]
+        lib.or_census_bm_sample.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, u64p, u64p, u64p]
         _lib = lib
     return _lib
 
@@ -129,19 +131,43 @@ def invariants(n: int, src, dst) -> dict:
     return dict(zip(("M", "A", "N", "out2", "in2", "paths", "triangles", "arcs"), v))
 
 
-def census_bm_sample(n: int, src, dst, stride: int, offset: int = 0):
-    """Time the Fig. 5 loop over vertices u = offset (mod stride).
+class SampledGraph:
+    """The oracle's graph built once, for repeated timing samples of the Fig. 5 loop."""
 
-    Returns (seconds, partial connected counts, merge work of the sample, total merge work).
-    """
-    s, d, ps, pd = _arcs(src, dst)
-    out = np.zeros(32, dtype=np.uint64)
-    ws = np.zeros(1, dtype=np.uint64)
-    wt = np.zeros(1, dtype=np.uint64)
-    sec = _load().or_census_bm_sample(n, len(s), ps, pd, stride, offset, _p64(out), _p64(ws), _p64(wt))
-    if sec < 0:
-        raise ValueError("vertex id out of range")
-    return sec, _u128(out, 16), int(ws[0]), int(wt[0])
+    def __init__(self, n: int, src, dst):
+        s, d, ps, pd = _arcs(src, dst)
+        self._h = _load().or_graph_new(n, len(s), ps, pd)
+        if not self._h:
+            raise ValueError("vertex id out of range")
+
+    def sample(self, stride: int, offset: int = 0):
+        """Time the loop over vertices u = offset (mod stride): (seconds, partial counts,
+        merge work of the sample, total merge work)."""
+        out = np.zeros(32, dtype=np.uint64)
+        ws = np.zeros(1, dtype=np.uint64)
+        wt = np.zeros(1, dtype=np.uint64)
+        sec = _load().or_census_bm_sample(self._h, stride, offset, _p64(out), _p64(ws), _p64(wt))
+        return sec, _u128(out, 16), int(ws[0]), int(wt[0])
+
+    def close(self):
+        if self._h:
+            _load().or_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def census_bm_sample(n: int, src, dst, stride: int, offset: int = 0):
+    """One timing sample (builds and frees the graph): see SampledGraph.sample."""
+    g = SampledGraph(n, src, dst)
+    try:
+        return g.sample(stride, offset)
+    finally:
+        g.close()
 
 
 def choose3(n: int) -> int:

@@ -352,24 +352,31 @@ int or_census_bm_parallel(uint32_t n, uint64_t m, const uint32_t* src, const uin
     return 0;
 }
 
-// Timing sample of the Fig. 5 census: runs steps 2.1 - 2.1.4 for the vertices u with
-// u % stride == offset only (no 003 step).  Returns the seconds spent in the census loop;
-// work_sample / work_total receive the merge length of the sample and of the whole graph.
-double or_census_bm_sample(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,
-                           uint32_t stride, uint32_t offset, uint64_t* out, uint64_t* work_sample,
-                           uint64_t* work_total) {
+// Timing samples of the Fig. 5 census on a graph built once (or_graph_new): runs steps
+// 2.1 - 2.1.4 for the vertices u with u % stride == offset only (no 003 step) and returns
+// the seconds spent in that loop; work_sample / work_total receive the merge length
+// (|N[u]| + |N[v]| over the pairs) of the sample and of the whole graph.
+void* or_graph_new(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst) {
     ensure_table();
-    Digraph g;
-    if (!build_digraph(n, m, src, dst, g)) return -1.0;
+    Digraph* g = new Digraph();
+    if (!build_digraph(n, m, src, dst, *g)) { delete g; return nullptr; }
+    return g;
+}
+
+void or_graph_free(void* h) { delete static_cast<Digraph*>(h); }
+
+double or_census_bm_sample(void* h, uint32_t stride, uint32_t offset, uint64_t* out, uint64_t* work_sample,
+                           uint64_t* work_total) {
+    const Digraph& g = *static_cast<Digraph*>(h);
     uint64_t tot = 0;
-    for (uint32_t u = 0; u < n; ++u)
+    for (uint32_t u = 0; u < g.n; ++u)
         for (const Tagged& tv : g.N[u])
             if (u < tv.id) tot += g.N[u].size() + g.N[tv.id].size();
     u128 census[16] = {};
     std::vector<SElem> S;
     double t0 = now_seconds();
     uint64_t w = 0;
-    for (uint32_t u = offset; u < n; u += stride) w += bm_vertex(g, u, census, S);
+    for (uint32_t u = offset; u < g.n; u += stride) w += bm_vertex(g, u, census, S);
     double t1 = now_seconds();
     store(census, out);
     *work_sample = w;
@@ -421,16 +428,21 @@ int or_invariants(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* d
         in2 += (u128)din[x] * (din[x] - (din[x] ? 1 : 0)) / 2;
         paths += (u128)din[x] * dout - mut;
     }
-    // triangles: for each undirected edge a<b, the common neighbours c>b
-    std::vector<std::vector<uint32_t>> und(n);
-    for (uint32_t x = 0; x < n; ++x)
-        for (const Tagged& t : g.N[x]) und[x].push_back(t.id);
+    // triangles, each once: orient every pair from lower to higher (degree, id) rank and
+    // count, for each oriented pair a->b, the common out-neighbours of a and b
+    std::vector<uint64_t> deg(n);
+    for (uint32_t x = 0; x < n; ++x) deg[x] = g.N[x].size();
+    auto before = [&](uint32_t x, uint32_t y) { return deg[x] < deg[y] || (deg[x] == deg[y] && x < y); };
+    std::vector<std::vector<uint32_t>> fwd(n);
+    for (uint32_t x = 0; x < n; ++x) {
+        for (const Tagged& t : g.N[x])
+            if (before(x, t.id)) fwd[x].push_back(t.id);
+        std::sort(fwd[x].begin(), fwd[x].end());
+    }
     for (uint32_t a = 0; a < n; ++a)
-        for (uint32_t b : und[a]) {
-            if (b <= a) continue;
-            auto ia = std::upper_bound(und[a].begin(), und[a].end(), b);
-            auto ib = std::upper_bound(und[b].begin(), und[b].end(), b);
-            while (ia != und[a].end() && ib != und[b].end()) {
+        for (uint32_t b : fwd[a]) {
+            auto ia = fwd[a].begin(), ib = fwd[b].begin();
+            while (ia != fwd[a].end() && ib != fwd[b].end()) {
                 if (*ia < *ib) ++ia; else if (*ib < *ia) ++ib; else { ++tri; ++ia; ++ib; }
             }
         }

@@ -1,0 +1,274 @@
+"""Python binding of libtc.so, the GB300 triad-census library (include/tc.h).
+
+Argument marshalling only: every step of the census runs in the library's CUDA kernels.
+The functions keep the C names (tc_graph_create_arcs, tc_census, ...).  Buffers may be
+numpy arrays (host) or CUDA tensors (device); a CUDA stream may be passed as an int handle,
+a torch.cuda.Stream, or None for torch's current stream.  Counts come back as Python ints.
+
+If libtc.so cannot be loaded this module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc.so")
+
+CLASS_NAMES = ("003", "012", "102", "021D", "021U", "021C", "111D", "111U",
+               "030T", "030C", "201", "120D", "120U", "120C", "210", "300")
+
+TC_OK, TC_ERR_ARG, TC_ERR_RANGE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_BUSY = range(7)
+TC_ALGO_UNION, TC_ALGO_SUFFIX = 0, 1
+TC_SCHED_PLAIN, TC_SCHED_LEARNED = 0, 1
+
+
+class TcError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {_status_name(status)}: {msg}")
+        self.status = status
+
+
+class tc_u128(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_uint64), ("hi", ctypes.c_uint64)]
+
+    def value(self) -> int:
+        return int(self.lo) | (int(self.hi) << 64)
+
+
+class tc_options(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_uint32), ("schedule", ctypes.c_uint32), ("warp_max_deg", ctypes.c_uint32),
+                ("chunk_entries", ctypes.c_uint32), ("item_work", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 10)]
+
+
+class tc_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("max_deg", ctypes.c_uint32), ("arcs", ctypes.c_uint64),
+                ("e_sym", ctypes.c_uint64), ("mutual", ctypes.c_uint64), ("loops_dropped", ctypes.c_uint64),
+                ("dups_dropped", ctypes.c_uint64), ("sum_d2", ctypes.c_uint64), ("sum_dv_upper", ctypes.c_uint64),
+                ("bytes_alg", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib = None
+_VP, _U32, _U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+
+# name -> (restype, argtypes); every symbol include/tc.h declares
+SIGNATURES = {
+    "tc_graph_create_arcs": (ctypes.c_int, [_U32, _U64, _VP, _VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(_VP)]),
+    "tc_graph_create_csr": (ctypes.c_int, [_U32, _VP, _VP, ctypes.c_int, _VP, _VP, ctypes.POINTER(_VP)]),
+    "tc_census": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(tc_u128)]),
+    "tc_census_opts": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(tc_u128)]),
+    "tc_census_async": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "tc_null_count": (tc_u128, [_U32, ctypes.POINTER(_U64)]),
+    "tc_census_batch": (ctypes.c_int, [_VP, _U32, _VP, ctypes.POINTER(_U64), ctypes.POINTER(tc_u128)]),
+    "tc_graph_stats": (ctypes.c_int, [_VP, ctypes.POINTER(tc_graph_info)]),
+    "tc_graph_device_csr": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "tc_graph_export_csr": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "tc_graph_destroy": (None, [_VP]),
+    "tc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "tc_last_error": (ctypes.c_char_p, []),
+    "tc_tricode_table": (None, [ctypes.POINTER(ctypes.c_uint8)]),
+}
+
+
+def load():
+    """Load libtc.so (built by _build.build() / __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1209_6308_gb300._build.build() "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _status_name(s: int) -> str:
+    names = ["TC_OK", "TC_ERR_ARG", "TC_ERR_RANGE", "TC_ERR_OOM", "TC_ERR_CUDA", "TC_ERR_TIMEOUT", "TC_ERR_BUSY"]
+    return names[s] if 0 <= s < len(names) else f"status {s}"
+
+
+def _check(status: int, where: str):
+    if status != TC_OK:
+        raise TcError(status, where, load().tc_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+def _buffer(x, dtype):
+    """(pointer, is_device, keepalive) for a numpy array or a CUDA tensor."""
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if x.element_size() != np.dtype(dtype).itemsize or not x.is_contiguous():
+            raise ValueError(f"tensor must be contiguous with {np.dtype(dtype).itemsize}-byte elements")
+        return x.data_ptr(), bool(x.is_cuda), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, False, a
+
+
+def _options(opts):
+    if opts is None:
+        return None, None
+    o = tc_options()
+    for k, v in dict(opts).items():
+        setattr(o, k, int(v))
+    return ctypes.addressof(o), o
+
+
+def tc_graph_create_arcs(n: int, src, dst, stream=None, options=None) -> int:
+    """Build a graph from arcs src[i] -> dst[i]; returns an opaque handle (int)."""
+    ps, ds, ka = _buffer(src, np.uint32)
+    pd, dd, kb = _buffer(dst, np.uint32)
+    m = len(ka) if hasattr(ka, "__len__") else ka.numel()
+    if (len(kb) if hasattr(kb, "__len__") else kb.numel()) != m:
+        raise ValueError("src and dst differ in length")
+    if ds != dd:
+        raise ValueError("src and dst must both be host or both be device buffers")
+    po, keep = _options(options)
+    out = _VP()
+    _check(load().tc_graph_create_arcs(n, m, ps, pd, int(ds), _stream_handle(stream), po, ctypes.byref(out)),
+           "tc_graph_create_arcs")
+    return out.value
+
+
+def tc_graph_create_csr(n: int, off, adj_flagged, stream=None, options=None) -> int:
+    """Build a graph from a canonical flagged CSR (off: uint64[n+1], adj: uint32)."""
+    po_, dev_o, ko = _buffer(off, np.uint64)
+    pa, dev_a, ka = _buffer(adj_flagged, np.uint32)
+    if dev_o != dev_a:
+        raise ValueError("off and adj must both be host or both be device buffers")
+    po, keep = _options(options)
+    out = _VP()
+    _check(load().tc_graph_create_csr(n, po_, pa, int(dev_o), _stream_handle(stream), po, ctypes.byref(out)),
+           "tc_graph_create_csr")
+    return out.value
+
+
+def tc_census(g: int, stream=None, options=None) -> list:
+    """Full 16-class census of a graph (synchronises the stream)."""
+    out = (tc_u128 * 16)()
+    po, keep = _options(options)
+    _check(load().tc_census_opts(g, _stream_handle(stream), po, out), "tc_census")
+    return [out[i].value() for i in range(16)]
+
+
+def tc_census_async(g: int, d_out16, stream=None, options=None) -> None:
+    """Enqueue a census writing counts 1..15 into a 16-element uint64 device buffer."""
+    p, dev, keep = _buffer(d_out16, np.uint64)
+    if not dev:
+        raise ValueError("d_out16 must be device memory")
+    po, keepo = _options(options)
+    _check(load().tc_census_async(g, _stream_handle(stream), po, p), "tc_census_async")
+
+
+def tc_null_count(n: int, counts16) -> int:
+    c = (ctypes.c_uint64 * 16)(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in counts16])
+    return load().tc_null_count(n, c).value()
+
+
+def tc_census_batch(graphs, stream=None) -> list:
+    """Census of many graphs: list of 16-int lists (index 0 is the full 128-bit null count)."""
+    k = len(graphs)
+    arr = (_VP * k)(*graphs)
+    out = (ctypes.c_uint64 * (16 * k))()
+    z = (tc_u128 * k)()
+    _check(load().tc_census_batch(ctypes.cast(arr, _VP), k, _stream_handle(stream), out, z), "tc_census_batch")
+    res = []
+    for i in range(k):
+        row = [int(out[16 * i + t]) for t in range(16)]
+        row[0] = z[i].value()
+        res.append(row)
+    return res
+
+
+def tc_graph_stats(g: int) -> dict:
+    info = tc_graph_info()
+    _check(load().tc_graph_stats(g, ctypes.byref(info)), "tc_graph_stats")
+    return info.as_dict()
+
+
+def tc_graph_device_csr(g: int):
+    """(off, adj, new_of_old) device pointers as ints."""
+    o, a, p = _VP(), _VP(), _VP()
+    _check(load().tc_graph_device_csr(g, ctypes.byref(o), ctypes.byref(a), ctypes.byref(p)), "tc_graph_device_csr")
+    return o.value, a.value, p.value
+
+
+def tc_graph_export_csr(g: int):
+    """(off uint64[n+1], adj uint32[2 e_sym], new_of_old uint32[n]) copied to host numpy arrays."""
+    st = tc_graph_stats(g)
+    n = st["n"]
+    off = np.zeros(n + 1, np.uint64)
+    adj = np.zeros(2 * st["e_sym"], np.uint32)
+    perm = np.zeros(n, np.uint32)
+    _check(load().tc_graph_export_csr(g, off.ctypes.data, adj.ctypes.data, perm.ctypes.data), "tc_graph_export_csr")
+    return off, adj, perm
+
+
+def tc_graph_destroy(g: int) -> None:
+    if g:
+        load().tc_graph_destroy(g)
+
+
+def tc_tricode_table() -> np.ndarray:
+    t = np.zeros(64, dtype=np.uint8)
+    load().tc_tricode_table(t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return t
+
+
+class Graph:
+    """Owning wrapper around a tc_graph handle."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle, self.n = handle, n
+
+    @classmethod
+    def from_arcs(cls, n, src, dst, stream=None, options=None):
+        return cls(tc_graph_create_arcs(n, src, dst, stream, options), n)
+
+    @classmethod
+    def from_csr(cls, n, off, adj, stream=None, options=None):
+        return cls(tc_graph_create_csr(n, off, adj, stream, options), n)
+
+    def census(self, stream=None, options=None):
+        return tc_census(self.handle, stream, options)
+
+    def stats(self):
+        return tc_graph_stats(self.handle)
+
+    def close(self):
+        tc_graph_destroy(self.handle)
+        self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.handle:
+                self.close()
+        except Exception:
+            pass

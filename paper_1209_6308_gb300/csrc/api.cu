@@ -1,0 +1,346 @@
+// api.cu - the C ABI declared in include/tc.h: graph lifecycle, census entry points and
+// the 128-bit null count of Fig. 5 steps 3-5.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "graph.cuh"
+
+struct tc_graph {
+    tc::GraphStore s;
+};
+
+namespace tc {
+
+namespace {
+thread_local std::string t_err;
+}
+
+void set_error(const std::string& msg) { t_err = msg; }
+
+tc_status fail(tc_status s, const std::string& msg) {
+    t_err = msg;
+    return s;
+}
+
+tc_status cuda_fail(cudaError_t e, const char* what) {
+    t_err = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return TC_ERR_OOM;
+    }
+    return TC_ERR_CUDA;
+}
+
+tc_status DevBuf::alloc(size_t b, cudaStream_t s) {
+    release();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMallocAsync(&p, b, s);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? TC_ERR_OOM : TC_ERR_CUDA,
+                    std::string("device allocation of ") + std::to_string(b) + " bytes: " + cudaGetErrorString(e));
+    }
+    bytes = b;
+    st = s;
+    async = true;
+    return TC_OK;
+}
+
+tc_status DevBuf::alloc_persistent(size_t b) {
+    release();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? TC_ERR_OOM : TC_ERR_CUDA,
+                    std::string("device allocation of ") + std::to_string(b) + " bytes: " + cudaGetErrorString(e));
+    }
+    bytes = b;
+    async = false;
+    return TC_OK;
+}
+
+void DevBuf::release() {
+    if (p) {
+        if (async) cudaFreeAsync(p, st);
+        else cudaFree(p);
+    }
+    p = nullptr;
+    bytes = 0;
+}
+
+int sm_count() {
+    int dev = 0, c = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    return c > 0 ? c : 1;
+}
+
+tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out) {
+    Opts o = base ? *base : Opts();
+    if (in) {
+        if (in->algo) o.algo = in->algo;
+        if (in->schedule) o.schedule = in->schedule;
+        if (in->warp_max_deg) o.warp_max_deg = in->warp_max_deg;
+        if (in->chunk_entries) o.chunk = in->chunk_entries;
+        if (in->item_work) o.item_work = in->item_work;
+        if (in->ctas_per_sm) o.ctas_per_sm = in->ctas_per_sm;
+    }
+    if (o.algo > TC_ALGO_SUFFIX) return fail(TC_ERR_ARG, "unknown algo");
+    if (o.schedule > TC_SCHED_LEARNED) return fail(TC_ERR_ARG, "unknown schedule");
+    if (o.chunk < 512 || o.chunk > 16384 || (o.chunk & (o.chunk - 1)))
+        return fail(TC_ERR_ARG, "chunk_entries must be a power of two in [512, 16384]");
+    if (o.warp_max_deg > o.chunk / 8) return fail(TC_ERR_ARG, "warp_max_deg must be <= chunk_entries / 8");
+    if (o.ctas_per_sm < 1 || o.ctas_per_sm > 8) return fail(TC_ERR_ARG, "ctas_per_sm must be in [1, 8]");
+    *out = o;
+    return TC_OK;
+}
+
+namespace {
+
+tc_status init_graph(tc_graph* g, uint32_t n, const tc_options* opt) {
+    g->s.n = n;
+    TC_TRY(resolve_opts(opt, nullptr, &g->s.opts));
+    TC_TRY(g->s.ctr.alloc_persistent(sizeof(uint32_t) * 4));
+    TC_TRY(g->s.acc.alloc_persistent(sizeof(unsigned long long) * 16));
+    TC_CUDA(cudaMallocHost(&g->s.h_counts, sizeof(unsigned long long) * 16));
+    return TC_OK;
+}
+
+void destroy(tc_graph* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    if (g->s.h_counts) cudaFreeHost(g->s.h_counts);
+    delete g;
+}
+
+// Host -> device copy of `count` elements into a stream-ordered buffer
+template <typename T>
+tc_status upload(const T* h, uint64_t count, DevBuf& b, cudaStream_t st) {
+    TC_TRY(b.alloc(sizeof(T) * (count ? count : 1), st));
+    if (count) TC_CUDA(cudaMemcpyAsync(b.p, h, sizeof(T) * count, cudaMemcpyHostToDevice, st));
+    return TC_OK;
+}
+
+tc_u128 to_u128(unsigned __int128 x) {
+    tc_u128 r;
+    r.lo = (uint64_t)x;
+    r.hi = (uint64_t)(x >> 64);
+    return r;
+}
+
+unsigned __int128 choose3(uint64_t n) {
+    if (n < 3) return 0;
+    unsigned __int128 a = n, b = n - 1, c = n - 2;
+    return a * b * c / 6;
+}
+
+}  // namespace
+}  // namespace tc
+
+using namespace tc;
+
+extern "C" {
+
+const char* tc_last_error(void) { return t_err.c_str(); }
+
+const char* tc_status_str(tc_status s) {
+    switch (s) {
+        case TC_OK: return "TC_OK";
+        case TC_ERR_ARG: return "TC_ERR_ARG";
+        case TC_ERR_RANGE: return "TC_ERR_RANGE";
+        case TC_ERR_OOM: return "TC_ERR_OOM";
+        case TC_ERR_CUDA: return "TC_ERR_CUDA";
+        case TC_ERR_TIMEOUT: return "TC_ERR_TIMEOUT";
+        case TC_ERR_BUSY: return "TC_ERR_BUSY";
+    }
+    return "TC_ERR_UNKNOWN";
+}
+
+void tc_tricode_table(uint8_t out[64]) {
+    const uint8_t* t = host_tricode_table();
+    if (t) std::memcpy(out, t, 64);
+    else std::memset(out, 0xff, 64);
+}
+
+tc_status tc_graph_create_arcs(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst, int ptr_is_device,
+                               void* stream, const tc_options* opt, tc_graph** out) {
+    if (!out) return fail(TC_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (m && (!src || !dst)) return fail(TC_ERR_ARG, "src/dst is null");
+    if (n > (1u << 30)) return fail(TC_ERR_RANGE, "n > 2^30 (ids carry two direction bits)");
+    cudaStream_t st = (cudaStream_t)stream;
+    tc_graph* g = new tc_graph();
+    tc_status s = init_graph(g, n, opt);
+    if (s == TC_OK) {
+        if (ptr_is_device) {
+            s = build_from_arcs(g->s, m, src, dst, st);
+        } else {
+            DevBuf ds, dd;
+            s = upload(src, m, ds, st);
+            if (s == TC_OK) s = upload(dst, m, dd, st);
+            if (s == TC_OK) s = build_from_arcs(g->s, m, ds.as<uint32_t>(), dd.as<uint32_t>(), st);
+        }
+    }
+    if (s == TC_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "graph build");
+    }
+    if (s != TC_OK) {
+        std::string keep = t_err;
+        destroy(g);
+        t_err = keep;
+        return s;
+    }
+    *out = g;
+    return TC_OK;
+}
+
+tc_status tc_graph_create_csr(uint32_t n, const uint64_t* off, const uint32_t* adj_flagged, int ptr_is_device,
+                              void* stream, const tc_options* opt, tc_graph** out) {
+    if (!out) return fail(TC_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!off) return fail(TC_ERR_ARG, "off is null");
+    if (n > (1u << 30)) return fail(TC_ERR_RANGE, "n > 2^30 (ids carry two direction bits)");
+    cudaStream_t st = (cudaStream_t)stream;
+    tc_graph* g = new tc_graph();
+    tc_status s = init_graph(g, n, opt);
+    if (s == TC_OK) {
+        if (ptr_is_device) {
+            s = build_from_csr(g->s, off, adj_flagged, st);
+        } else {
+            uint64_t total = off[n];
+            if (off[0] != 0 || (total && !adj_flagged)) s = fail(TC_ERR_ARG, "malformed CSR offsets");
+            for (uint32_t x = 0; s == TC_OK && x < n; ++x)
+                if (off[x + 1] < off[x]) s = fail(TC_ERR_ARG, "CSR offsets decrease");
+            DevBuf doff, dadj;
+            if (s == TC_OK) s = upload(off, (uint64_t)n + 1, doff, st);
+            if (s == TC_OK) s = upload(adj_flagged, total, dadj, st);
+            if (s == TC_OK) s = build_from_csr(g->s, doff.as<uint64_t>(), dadj.as<uint32_t>(), st);
+        }
+    }
+    if (s == TC_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "graph build");
+    }
+    if (s != TC_OK) {
+        std::string keep = t_err;
+        destroy(g);
+        t_err = keep;
+        return s;
+    }
+    *out = g;
+    return TC_OK;
+}
+
+void tc_graph_destroy(tc_graph* g) { destroy(g); }
+
+tc_status tc_graph_stats(const tc_graph* g, tc_graph_info* info) {
+    if (!g || !info) return fail(TC_ERR_ARG, "null argument");
+    const GraphStore& s = g->s;
+    info->n = s.n;
+    info->max_deg = s.max_deg;
+    info->arcs = s.arcs;
+    info->e_sym = s.e_sym;
+    info->mutual = s.mutual;
+    info->loops_dropped = s.loops;
+    info->dups_dropped = s.dups;
+    info->sum_d2 = s.sum_d2;
+    info->sum_dv_upper = s.sum_dv_upper;
+    info->bytes_alg = 8ull * (s.n + 1ull) + 8ull * s.e_sym + 4ull * s.sum_dv_upper + 16ull * s.e_sym + 128ull;
+    return TC_OK;
+}
+
+tc_status tc_graph_device_csr(const tc_graph* g, const uint64_t** off, const uint32_t** adj,
+                              const uint32_t** new_of_old) {
+    if (!g) return fail(TC_ERR_ARG, "null graph");
+    if (off) *off = g->s.off.as<uint64_t>();
+    if (adj) *adj = g->s.adj.as<uint32_t>();
+    if (new_of_old) *new_of_old = g->s.new_of_old.as<uint32_t>();
+    return TC_OK;
+}
+
+tc_status tc_graph_export_csr(const tc_graph* g, uint64_t* off_host, uint32_t* adj_host, uint32_t* new_of_old_host) {
+    if (!g) return fail(TC_ERR_ARG, "null graph");
+    const GraphStore& s = g->s;
+    TC_CUDA(cudaDeviceSynchronize());
+    if (off_host) TC_CUDA(cudaMemcpy(off_host, s.off.p, sizeof(uint64_t) * (s.n + 1ull), cudaMemcpyDeviceToHost));
+    if (adj_host && s.e_sym) TC_CUDA(cudaMemcpy(adj_host, s.adj.p, sizeof(uint32_t) * 2ull * s.e_sym, cudaMemcpyDeviceToHost));
+    if (new_of_old_host && s.n) TC_CUDA(cudaMemcpy(new_of_old_host, s.new_of_old.p, sizeof(uint32_t) * s.n, cudaMemcpyDeviceToHost));
+    return TC_OK;
+}
+
+tc_u128 tc_null_count(uint32_t n, const uint64_t counts16[16]) {
+    unsigned __int128 sum = 0;
+    for (int t = 1; t < 16; ++t) sum += counts16[t];
+    return to_u128(choose3(n) - sum);
+}
+
+tc_status tc_census_async(tc_graph* g, void* stream, const tc_options* opt, uint64_t* d_out16) {
+    if (!g || !d_out16) return fail(TC_ERR_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    Opts o;
+    TC_TRY(resolve_opts(opt, &g->s.opts, &o));
+    std::unique_lock<std::mutex> lk(g->s.busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(TC_ERR_BUSY, "graph is in use by another call");
+    Plan* p = nullptr;
+    TC_TRY(get_plan(g->s, o, st, &p));
+    TC_CUDA(cudaMemsetAsync(d_out16, 0, sizeof(uint64_t) * 16, st));
+    return census_enqueue(g->s, o, *p, st, reinterpret_cast<unsigned long long*>(d_out16));
+}
+
+tc_status tc_census_opts(tc_graph* g, void* stream, const tc_options* opt, tc_u128 out[16]) {
+    if (!g || !out) return fail(TC_ERR_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    Opts o;
+    TC_TRY(resolve_opts(opt, &g->s.opts, &o));
+    std::unique_lock<std::mutex> lk(g->s.busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(TC_ERR_BUSY, "graph is in use by another call");
+    Plan* p = nullptr;
+    TC_TRY(get_plan(g->s, o, st, &p));
+    TC_CUDA(cudaMemsetAsync(g->s.acc.p, 0, sizeof(unsigned long long) * 16, st));
+    TC_TRY(census_enqueue(g->s, o, *p, st, g->s.acc.as<unsigned long long>()));
+    TC_CUDA(cudaMemcpyAsync(g->s.h_counts, g->s.acc.p, sizeof(unsigned long long) * 16, cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    uint64_t c[16];
+    for (int t = 0; t < 16; ++t) c[t] = g->s.h_counts[t];
+    c[0] = 0;
+    out[0] = tc_null_count(g->s.n, c);
+    for (int t = 1; t < 16; ++t) { out[t].lo = c[t]; out[t].hi = 0; }
+    return TC_OK;
+}
+
+tc_status tc_census(tc_graph* g, void* stream, tc_u128 out[16]) { return tc_census_opts(g, stream, nullptr, out); }
+
+// Per-graph launches on one stream into one device array, one copy back (the batched
+// persistent form lives in batch.cu when built; this is the reference loop).
+tc_status tc_census_batch(tc_graph* const* gs, uint32_t k, void* stream, uint64_t* out16xk, tc_u128* out003_k) {
+    if (!gs || !out16xk) return fail(TC_ERR_ARG, "null argument");
+    if (k == 0) return TC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf d;
+    TC_TRY(d.alloc(sizeof(unsigned long long) * 16ull * k, st));
+    TC_CUDA(cudaMemsetAsync(d.p, 0, sizeof(unsigned long long) * 16ull * k, st));
+    for (uint32_t i = 0; i < k; ++i) {
+        if (!gs[i]) return fail(TC_ERR_ARG, "null graph in batch");
+        Opts o = gs[i]->s.opts;
+        Plan* p = nullptr;
+        TC_TRY(get_plan(gs[i]->s, o, st, &p));
+        TC_TRY(census_enqueue(gs[i]->s, o, *p, st, d.as<unsigned long long>() + 16ull * i));
+    }
+    TC_CUDA(cudaMemcpyAsync(out16xk, d.p, sizeof(unsigned long long) * 16ull * k, cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    for (uint32_t i = 0; i < k; ++i) {
+        uint64_t* c = out16xk + 16ull * i;
+        c[0] = 0;
+        tc_u128 z = tc_null_count(gs[i]->s.n, c);
+        c[0] = z.lo;
+        if (out003_k) out003_k[i] = z;
+    }
+    return TC_OK;
+}
+
+}  // extern "C"

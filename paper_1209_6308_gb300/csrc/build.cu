@@ -1,0 +1,382 @@
+// build.cu - device construction of the compact graph structure of Sec. 6 (Fig. 7):
+// one edge array holding every vertex's sorted neighbour list, a start offset per vertex,
+// and the two low bits of each stored id giving the arc direction (01 owner->neighbour,
+// 10 neighbour->owner, 11 both).
+//
+// From an arc list: validate ids, drop self-loops, key each arc by its unordered pair with
+// one direction bit, radix sort, merge equal pairs by OR-ing their direction bits, count
+// degrees, relabel vertices by descending degree (ties by original id), emit both
+// directions of every pair in the new ids, radix sort by (owner, neighbour), and read off
+// the offsets.  A CSR input is validated (sorted, flagged, loop-free, symmetric) and then
+// goes through the same relabel.
+#include <algorithm>
+
+#include "graph.cuh"
+#include "tc_internal.cuh"
+
+namespace tc {
+namespace {
+
+constexpr int kB = 256;
+
+__device__ __forceinline__ uint32_t swap_dir(uint32_t d) { return ((d & 1u) << 1) | ((d >> 1) & 1u); }
+
+// stats[0] self-loops, stats[1] ids out of range
+__global__ void k_make_keys(const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t n, int B,
+                            uint64_t* keys, unsigned long long* stats) {
+    uint32_t loops = 0, bad = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t a = src[i], b = dst[i];
+        uint64_t key = ~0ull;
+        if (a >= n || b >= n) ++bad;
+        else if (a == b) ++loops;
+        else {
+            uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+            uint64_t dir = a < b ? 1u : 2u;           // 01: lo->hi, 10: hi->lo
+            key = (lo << (B + 2)) | (hi << 2) | dir;
+        }
+        keys[i] = key;
+    }
+    for (int o = 16; o; o >>= 1) {
+        loops += __shfl_xor_sync(0xffffffffu, loops, o);
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (loops) atomicAdd(&stats[0], (unsigned long long)loops);
+        if (bad) atomicAdd(&stats[1], (unsigned long long)bad);
+    }
+}
+
+__global__ void k_head_flags(const uint64_t* keys, uint64_t cnt, uint32_t* flag) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x)
+        flag[i] = (i == 0 || (keys[i] >> 2) != (keys[i - 1] >> 2)) ? 1u : 0u;
+}
+
+// Runs of equal pairs -> one pair key (lo<<B | hi) and the OR of their direction bits.
+__global__ void k_unique(const uint64_t* keys, uint64_t cnt, const uint32_t* flag, const uint32_t* pos,
+                         uint64_t* ukey, uint32_t* udir) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t r = pos[i] + flag[i] - 1u;
+        if (flag[i]) ukey[r] = keys[i] >> 2;
+        atomicOr(&udir[r], (uint32_t)(keys[i] & 3u));
+    }
+}
+
+// degrees; stats[2] mutual pairs
+__global__ void k_degrees(const uint64_t* ukey, const uint32_t* udir, uint64_t E, int B, uint32_t* deg,
+                          unsigned long long* stats) {
+    const uint64_t mask = (1ull << B) - 1;
+    uint32_t mut = 0;
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < E; r += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = ukey[r];
+        atomicAdd(&deg[k >> B], 1u);
+        atomicAdd(&deg[k & mask], 1u);
+        mut += (udir[r] == 3u);
+    }
+    for (int o = 16; o; o >>= 1) mut += __shfl_xor_sync(0xffffffffu, mut, o);
+    if ((threadIdx.x & 31) == 0 && mut) atomicAdd(&stats[2], (unsigned long long)mut);
+}
+
+__global__ void k_relabel_keys(const uint32_t* deg, uint32_t n, int B, uint64_t* rk) {
+    const uint64_t top = (1ull << B) - 1;
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x)
+        rk[x] = ((top - deg[x]) << B) | x;
+}
+
+__global__ void k_perm(const uint64_t* rk, uint32_t n, int B, const uint32_t* deg, uint32_t* new_of_old,
+                       uint32_t* new_deg) {
+    const uint64_t mask = (1ull << B) - 1;
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)(rk[r] & mask);
+        new_of_old[x] = (uint32_t)r;
+        new_deg[r] = deg[x];
+    }
+}
+
+// Both directions of each pair in the new ids: (owner << (B+2)) | (nbr << 2) | dir(owner).
+__global__ void k_entries(const uint64_t* ukey, const uint32_t* udir, uint64_t E, int B, const uint32_t* new_of_old,
+                          uint64_t* ek) {
+    const uint64_t mask = (1ull << B) - 1;
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < E; r += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = ukey[r];
+        uint64_t a = new_of_old[k >> B], b = new_of_old[k & mask];
+        uint32_t d = udir[r];
+        ek[2 * r] = (a << (B + 2)) | (b << 2) | d;
+        ek[2 * r + 1] = (b << (B + 2)) | (a << 2) | swap_dir(d);
+    }
+}
+
+__global__ void k_adj_from_entries(const uint64_t* ek, uint64_t cnt, int B, uint32_t* adj) {
+    const uint64_t mask = (1ull << (B + 2)) - 1;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x)
+        adj[i] = (uint32_t)(ek[i] & mask);
+}
+
+// up[x] = number of neighbours with id < x (lists ascend, so a lower_bound).
+__global__ void k_up(const uint64_t* off, const uint32_t* adj, uint32_t n, uint32_t* up) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t lo = off[x], hi = off[x + 1], b = lo;
+        uint32_t key = (uint32_t)x << 2;
+        while (lo < hi) {
+            uint64_t mid = (lo + hi) >> 1;
+            if (adj[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        up[x] = (uint32_t)(lo - b);
+    }
+}
+
+// stats[3] sum deg^2, stats[4] sum over upper pairs of deg(v), stats[5] max degree,
+// stats[7] vertices with deg > 0
+__global__ void k_graph_sums(const uint64_t* off, const uint32_t* adj, const uint32_t* up, uint32_t n,
+                             unsigned long long* stats) {
+    unsigned long long d2 = 0, dv = 0;
+    uint32_t mx = 0, act = 0;
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t d = off[x + 1] - off[x];
+        d2 += d * d;
+        mx = max(mx, (uint32_t)d);
+        act += (d > 0);
+        // x is the v of every pair (u, x) with u < x: the first up[x] neighbours
+        dv += (unsigned long long)up[x] * d;
+    }
+    for (int o = 16; o; o >>= 1) {
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        dv += __shfl_xor_sync(0xffffffffu, dv, o);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        act += __shfl_xor_sync(0xffffffffu, act, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (act) atomicAdd(&stats[7], (unsigned long long)act);
+        atomicAdd(&stats[3], d2);
+        atomicAdd(&stats[4], dv);
+        atomicMax(&stats[5], (unsigned long long)mx);
+    }
+}
+
+// ---- CSR input validation: stats[6] = number of violations
+__global__ void k_check_csr(const uint64_t* off, const uint32_t* adj, uint32_t n, uint64_t total,
+                            unsigned long long* stats) {
+    uint32_t badc = 0;
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t b = off[x], e = off[x + 1];
+        if (e < b || e > total) { ++badc; continue; }
+        for (uint64_t i = b; i < e; ++i) {
+            uint32_t w = adj[i], id = w >> 2, d = w & 3u;
+            if (id >= n || id == x || d == 0 || (i > b && (adj[i - 1] >> 2) >= id)) { ++badc; break; }
+            // symmetry: x must appear in N[id] with mirrored direction bits
+            uint64_t lo = off[id], hi = off[id + 1];
+            if (hi < lo || hi > total) { ++badc; break; }
+            uint32_t key = (uint32_t)x << 2;
+            while (lo < hi) {
+                uint64_t mid = (lo + hi) >> 1;
+                if ((adj[mid] & ~3u) < key) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= off[id + 1] || adj[lo] != (key | swap_dir(d))) { ++badc; break; }
+        }
+    }
+    for (int o = 16; o; o >>= 1) badc += __shfl_xor_sync(0xffffffffu, badc, o);
+    if ((threadIdx.x & 31) == 0 && badc) atomicAdd(&stats[6], (unsigned long long)badc);
+}
+
+// Upper entries (x < id) of a valid CSR -> pair keys and direction bits relative to lo = x.
+__global__ void k_csr_pairs(const uint64_t* off, const uint32_t* adj, uint32_t n, int B, const uint32_t* upos,
+                            uint64_t* ukey, uint32_t* udir, uint32_t* deg, unsigned long long* stats) {
+    uint32_t mut = 0;
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t b = off[x], e = off[x + 1];
+        deg[x] = (uint32_t)(e - b);
+        uint32_t r = upos[x];
+        for (uint64_t i = b; i < e; ++i) {
+            uint32_t w = adj[i], id = w >> 2;
+            if (id > x) {
+                ukey[r] = ((uint64_t)x << B) | id;
+                udir[r] = w & 3u;
+                mut += ((w & 3u) == 3u);
+                ++r;
+            }
+        }
+    }
+    for (int o = 16; o; o >>= 1) mut += __shfl_xor_sync(0xffffffffu, mut, o);
+    if ((threadIdx.x & 31) == 0 && mut) atomicAdd(&stats[2], (unsigned long long)mut);
+}
+
+__global__ void k_upper_counts(const uint64_t* off, const uint32_t* adj, uint32_t n, uint32_t* cnt) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t c = 0;
+        for (uint64_t i = off[x]; i < off[x + 1]; ++i) c += ((adj[i] >> 2) > x);
+        cnt[x] = c;
+    }
+}
+
+int bits_for(uint32_t n) {
+    int B = 1;
+    while ((1ull << B) < n) ++B;
+    return B;
+}
+
+// Steps shared by both inputs: E unique pairs (ukey = lo<<B | hi, udir relative to lo) and
+// degrees -> relabel, CSR, up[], stats.
+tc_status finish_graph(GraphStore& g, uint64_t E, int B, uint64_t* ukey, uint32_t* udir, uint32_t* deg,
+                       DevBuf& stats, cudaStream_t st) {
+    const uint32_t n = g.n;
+    const unsigned gridE = grid_for(E, kB, 1u << 16), gridN = grid_for(n, kB, 1u << 16);
+    // relabel by descending degree
+    DevBuf rk, rtmp, ndeg;
+    TC_TRY(rk.alloc(sizeof(uint64_t) * n, st));
+    TC_TRY(rtmp.alloc(sizeof(uint64_t) * n, st));
+    TC_TRY(ndeg.alloc(sizeof(uint32_t) * n, st));
+    TC_TRY(g.new_of_old.alloc_persistent(sizeof(uint32_t) * n));
+    k_relabel_keys<<<gridN, kB, 0, st>>>(deg, n, B, rk.as<uint64_t>());
+    TC_LAUNCH("k_relabel_keys");
+    uint64_t* kp = rk.as<uint64_t>();
+    uint64_t* tp = rtmp.as<uint64_t>();
+    TC_TRY(radix_sort_u64(&kp, &tp, n, 0, 2 * B, st));
+    k_perm<<<gridN, kB, 0, st>>>(kp, n, B, deg, g.new_of_old.as<uint32_t>(), ndeg.as<uint32_t>());
+    TC_LAUNCH("k_perm");
+    rk.release();
+    rtmp.release();
+    // offsets
+    TC_TRY(g.off.alloc_persistent(sizeof(uint64_t) * (n + 1ull)));
+    TC_TRY(scan_u32_to_u64(ndeg.as<uint32_t>(), g.off.as<uint64_t>(), n, st));
+    // entries in new ids, sorted by (owner, neighbour)
+    uint64_t total = 2 * E;
+    DevBuf ek, etmp;
+    TC_TRY(ek.alloc(sizeof(uint64_t) * (total ? total : 1), st));
+    TC_TRY(etmp.alloc(sizeof(uint64_t) * (total ? total : 1), st));
+    if (E) {
+        k_entries<<<gridE, kB, 0, st>>>(ukey, udir, E, B, g.new_of_old.as<uint32_t>(), ek.as<uint64_t>());
+        TC_LAUNCH("k_entries");
+    }
+    kp = ek.as<uint64_t>();
+    tp = etmp.as<uint64_t>();
+    TC_TRY(radix_sort_u64(&kp, &tp, total, 2, 2 * B + 2, st));
+    TC_TRY(g.adj.alloc_persistent(sizeof(uint32_t) * (total ? total : 1)));
+    if (total) {
+        k_adj_from_entries<<<grid_for(total, kB, 1u << 16), kB, 0, st>>>(kp, total, B, g.adj.as<uint32_t>());
+        TC_LAUNCH("k_adj_from_entries");
+    }
+    ek.release();
+    etmp.release();
+    TC_TRY(g.up.alloc_persistent(sizeof(uint32_t) * n));
+    k_up<<<gridN, kB, 0, st>>>(g.off.as<uint64_t>(), g.adj.as<uint32_t>(), n, g.up.as<uint32_t>());
+    TC_LAUNCH("k_up");
+    k_graph_sums<<<gridN, kB, 0, st>>>(g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(), n,
+                                       stats.as<unsigned long long>());
+    TC_LAUNCH("k_graph_sums");
+    unsigned long long hs[8];
+    TC_CUDA(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    g.e_sym = E;
+    g.mutual = hs[2];
+    g.arcs = E + hs[2];
+    g.sum_d2 = hs[3];
+    g.sum_dv_upper = hs[4];
+    g.max_deg = (uint32_t)hs[5];
+    g.loops = hs[0];
+    // degrees descend with the new id, so the vertices with deg > 0 are [0, n_active)
+    g.n_active = (uint32_t)hs[7];
+    return TC_OK;
+}
+
+}  // namespace
+
+tc_status build_from_arcs(GraphStore& g, uint64_t m, const uint32_t* d_src, const uint32_t* d_dst, cudaStream_t st) {
+    const uint32_t n = g.n;
+    const int B = bits_for(n);
+    if (m >= (1ull << 32)) return fail(TC_ERR_RANGE, "more than 2^32-1 arcs");
+    DevBuf stats, keys, tmp;
+    TC_TRY(stats.alloc(sizeof(unsigned long long) * 8, st));
+    TC_CUDA(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * 8, st));
+    TC_TRY(keys.alloc(sizeof(uint64_t) * (m ? m : 1), st));
+    TC_TRY(tmp.alloc(sizeof(uint64_t) * (m ? m : 1), st));
+    if (m) {
+        k_make_keys<<<grid_for(m, kB, 1u << 16), kB, 0, st>>>(d_src, d_dst, m, n, B, keys.as<uint64_t>(),
+                                                               stats.as<unsigned long long>());
+        TC_LAUNCH("k_make_keys");
+    }
+    unsigned long long hs[2];
+    TC_CUDA(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    if (hs[1]) return fail(TC_ERR_RANGE, "arc list holds a vertex id >= n");
+    uint64_t mv = m - hs[0];
+    uint64_t* kp = keys.as<uint64_t>();
+    uint64_t* tp = tmp.as<uint64_t>();
+    TC_TRY(radix_sort_u64(&kp, &tp, m, 2, 2 * B + 2, st));
+    // unique pairs
+    DevBuf flag, pos, ukey, udir, deg, total;
+    TC_TRY(flag.alloc(sizeof(uint32_t) * (mv ? mv : 1), st));
+    TC_TRY(pos.alloc(sizeof(uint32_t) * (mv ? mv : 1), st));
+    TC_TRY(total.alloc(sizeof(uint32_t), st));
+    uint32_t E = 0;
+    if (mv) {
+        k_head_flags<<<grid_for(mv, kB, 1u << 16), kB, 0, st>>>(kp, mv, flag.as<uint32_t>());
+        TC_LAUNCH("k_head_flags");
+        TC_TRY(scan_u32(flag.as<uint32_t>(), pos.as<uint32_t>(), mv, total.as<uint32_t>(), st));
+        TC_CUDA(cudaMemcpyAsync(&E, total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+    }
+    TC_TRY(ukey.alloc(sizeof(uint64_t) * (E ? E : 1), st));
+    TC_TRY(udir.alloc(sizeof(uint32_t) * (E ? E : 1), st));
+    TC_CUDA(cudaMemsetAsync(udir.p, 0, sizeof(uint32_t) * (E ? E : 1), st));
+    if (mv) {
+        k_unique<<<grid_for(mv, kB, 1u << 16), kB, 0, st>>>(kp, mv, flag.as<uint32_t>(), pos.as<uint32_t>(),
+                                                             ukey.as<uint64_t>(), udir.as<uint32_t>());
+        TC_LAUNCH("k_unique");
+    }
+    keys.release();
+    tmp.release();
+    flag.release();
+    pos.release();
+    TC_TRY(deg.alloc(sizeof(uint32_t) * n, st));
+    TC_CUDA(cudaMemsetAsync(deg.p, 0, sizeof(uint32_t) * n, st));
+    if (E) {
+        k_degrees<<<grid_for(E, kB, 1u << 16), kB, 0, st>>>(ukey.as<uint64_t>(), udir.as<uint32_t>(), E, B,
+                                                             deg.as<uint32_t>(), stats.as<unsigned long long>());
+        TC_LAUNCH("k_degrees");
+    }
+    TC_TRY(finish_graph(g, E, B, ukey.as<uint64_t>(), udir.as<uint32_t>(), deg.as<uint32_t>(), stats, st));
+    g.dups = m - g.loops - g.arcs;
+    return TC_OK;
+}
+
+tc_status build_from_csr(GraphStore& g, const uint64_t* d_off, const uint32_t* d_adj, cudaStream_t st) {
+    const uint32_t n = g.n;
+    const int B = bits_for(n);
+    uint64_t total_h = 0, first = 0;
+    TC_CUDA(cudaMemcpyAsync(&total_h, d_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaMemcpyAsync(&first, d_off, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    if (first != 0) return fail(TC_ERR_ARG, "CSR offsets must start at 0");
+    if (total_h & 1) return fail(TC_ERR_ARG, "CSR is not symmetric (odd number of entries)");
+    if (total_h >= (1ull << 32)) return fail(TC_ERR_RANGE, "more than 2^32-1 CSR entries");
+    DevBuf stats;
+    TC_TRY(stats.alloc(sizeof(unsigned long long) * 8, st));
+    TC_CUDA(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * 8, st));
+    const unsigned gridN = grid_for(n, kB, 1u << 16);
+    k_check_csr<<<gridN, kB, 0, st>>>(d_off, d_adj, n, total_h, stats.as<unsigned long long>());
+    TC_LAUNCH("k_check_csr");
+    unsigned long long hs[8];
+    TC_CUDA(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    if (hs[6]) return fail(TC_ERR_ARG, "CSR is not canonical (unsorted, loop, zero direction, id >= n or asymmetric)");
+    uint64_t E = total_h / 2;
+    DevBuf cnt, upos, ukey, udir, deg, etot;
+    TC_TRY(cnt.alloc(sizeof(uint32_t) * n, st));
+    TC_TRY(upos.alloc(sizeof(uint32_t) * n, st));
+    TC_TRY(etot.alloc(sizeof(uint32_t), st));
+    k_upper_counts<<<gridN, kB, 0, st>>>(d_off, d_adj, n, cnt.as<uint32_t>());
+    TC_LAUNCH("k_upper_counts");
+    TC_TRY(scan_u32(cnt.as<uint32_t>(), upos.as<uint32_t>(), n, etot.as<uint32_t>(), st));
+    TC_TRY(ukey.alloc(sizeof(uint64_t) * (E ? E : 1), st));
+    TC_TRY(udir.alloc(sizeof(uint32_t) * (E ? E : 1), st));
+    TC_TRY(deg.alloc(sizeof(uint32_t) * n, st));
+    k_csr_pairs<<<gridN, kB, 0, st>>>(d_off, d_adj, n, B, upos.as<uint32_t>(), ukey.as<uint64_t>(),
+                                      udir.as<uint32_t>(), deg.as<uint32_t>(), stats.as<unsigned long long>());
+    TC_LAUNCH("k_csr_pairs");
+    TC_TRY(finish_graph(g, E, B, ukey.as<uint64_t>(), udir.as<uint32_t>(), deg.as<uint32_t>(), stats, st));
+    g.dups = 0;
+    g.loops = 0;
+    return TC_OK;
+}
+
+}  // namespace tc

@@ -1,0 +1,75 @@
+// graph.cuh - the tc_graph object: device CSR (Sec. 6, Fig. 7), statistics, cached census
+// plans and the per-graph census workspace.
+#pragma once
+
+#include <mutex>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+
+// Resolved census options (defaults filled in).
+struct Opts {
+    uint32_t algo = TC_ALGO_UNION;
+    uint32_t schedule = TC_SCHED_PLAIN;
+    uint32_t warp_max_deg = 64;
+    uint32_t chunk = 4096;
+    uint32_t item_work = 1u << 18;
+    uint32_t ctas_per_sm = 3;
+    bool operator==(const Opts& o) const {
+        return algo == o.algo && schedule == o.schedule && warp_max_deg == o.warp_max_deg && chunk == o.chunk &&
+               item_work == o.item_work && ctas_per_sm == o.ctas_per_sm;
+    }
+};
+
+tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out);
+
+// A census plan: the CTA work items for the vertices with deg > warp_max_deg, and the
+// id range of the vertices handled one warp per vertex.
+struct Plan {
+    bool valid = false;
+    Opts key;
+    DevBuf items;
+    uint32_t n_items = 0;
+    uint32_t warp_begin = 0, warp_end = 0;
+};
+
+struct GraphStore {
+    uint32_t n = 0, n_active = 0, max_deg = 0;
+    uint64_t arcs = 0, e_sym = 0, mutual = 0, loops = 0, dups = 0, sum_d2 = 0, sum_dv_upper = 0;
+    DevBuf off, adj, up, new_of_old;
+    DevBuf ctr;        // census work counters (uint32 x 4)
+    DevBuf acc;        // census accumulators (uint64 x 16)
+    DevBuf cost;       // optional per-vertex predicted cost (float x n) for the learned schedule
+    Opts opts;
+    static constexpr int kPlans = 4;
+    Plan plans[kPlans];
+    int next_plan = 0;
+    unsigned long long* h_counts = nullptr;   // pinned staging for 16 counts
+    std::mutex busy;
+
+    GraphDev dev() const {
+        GraphDev d;
+        d.n = n;
+        d.n_active = n_active;
+        d.off = off.as<uint64_t>();
+        d.adj = adj.as<uint32_t>();
+        d.up = up.as<uint32_t>();
+        return d;
+    }
+};
+
+tc_status build_from_arcs(GraphStore& g, uint64_t m, const uint32_t* d_src, const uint32_t* d_dst, cudaStream_t st);
+tc_status build_from_csr(GraphStore& g, const uint64_t* d_off, const uint32_t* d_adj, cudaStream_t st);
+
+// Enqueue one census on `st`; counts of classes 1..15 are added to d_out16 (which the
+// caller zeroes; index 0 is never touched).  No host synchronisation, no allocation once
+// the plan for `o` exists (get_plan allocates it on first use).
+tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out);
+tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16);
+
+// The library's tricode -> class table (derived in tables.cu); census.cu copies it into
+// its device memory before the first census.
+const uint8_t* host_tricode_table();
+
+}  // namespace tc

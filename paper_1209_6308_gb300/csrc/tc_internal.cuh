@@ -1,0 +1,88 @@
+// tc_internal.cuh - shared declarations of the GPU triad-census library (device structs,
+// error plumbing, primitive launchers).  Only the library's own .cu files include this.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tc.h"
+
+namespace tc {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+tc_status fail(tc_status s, const std::string& msg);
+tc_status cuda_fail(cudaError_t e, const char* what);
+
+#define TC_CUDA(call)                                                     \
+    do {                                                                  \
+        cudaError_t _e = (call);                                          \
+        if (_e != cudaSuccess) return ::tc::cuda_fail(_e, #call);         \
+    } while (0)
+#define TC_LAUNCH(what)                                                   \
+    do {                                                                  \
+        cudaError_t _e = cudaGetLastError();                              \
+        if (_e != cudaSuccess) return ::tc::cuda_fail(_e, what);          \
+    } while (0)
+#define TC_TRY(expr)                                                      \
+    do {                                                                  \
+        tc_status _s = (expr);                                            \
+        if (_s != TC_OK) return _s;                                       \
+    } while (0)
+
+// Device buffer: alloc() is stream-ordered (freed on the same stream when released),
+// alloc_persistent() is a plain cudaMalloc for buffers that outlive the creating stream.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t st = nullptr;
+    bool async = false;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    tc_status alloc(size_t b, cudaStream_t s);
+    tc_status alloc_persistent(size_t b);
+    void release();
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------------ graph on the device
+// Compact CSR of Sec. 6 (Fig. 7) in degree-descending ids: adj entries are (id << 2) | dir
+// with dir bit 0 = owner->id and bit 1 = id->owner; lists ascend by id.
+struct GraphDev {
+    uint32_t n;
+    uint32_t n_active;      // vertices with deg > 0 are exactly ids [0, n_active)
+    const uint64_t* off;    // [n+1]
+    const uint32_t* adj;    // [off[n]]
+    const uint32_t* up;     // [n] number of neighbours with a smaller id (index of first v > u)
+};
+
+// One CTA work item of the census: vertex u, the chunk [a0, a1) of N[u] staged in shared
+// memory, and the pairs (u, N[u][j]) for j in [j0, j1) (all with N[u][j] > u).
+struct Item {
+    uint32_t u, a0, a1, j0, j1;
+};
+
+// ------------------------------------------------------------------ primitives
+// Exclusive scan of n uint32 values into uint32 (out may alias nothing); *total (device
+// pointer, may be null) receives the sum.
+tc_status scan_u32(const uint32_t* in, uint32_t* out, uint64_t n, uint32_t* total, cudaStream_t st);
+// Exclusive scan of n uint32 values into uint64 offsets; out has n+1 entries (out[n] = sum).
+tc_status scan_u32_to_u64(const uint32_t* in, uint64_t* out, uint64_t n, cudaStream_t st);
+// Stable LSD radix sort of n 64-bit keys on bits [lo_bit, hi_bit); keys and tmp both hold n
+// keys; the result ends in *keys (the pointers may be swapped).  n must be < 2^32.
+tc_status radix_sort_u64(uint64_t** keys, uint64_t** tmp, uint64_t n, int lo_bit, int hi_bit, cudaStream_t st);
+
+inline unsigned grid_for(uint64_t n, unsigned block, unsigned cap = 1u << 20) {
+    uint64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+int sm_count();
+
+}  // namespace tc

@@ -1,0 +1,93 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads, exports every
+function include/tc.h declares, and its host-only helpers are right."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tc.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tc_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1209_6308_gb300 import _build
+    _build.build()
+    import paper_1209_6308_gb300 as tc
+    return tc.load()
+
+
+def test_header_declares_the_census_entry_points():
+    names = _declared_functions()
+    for must in ("tc_graph_create_arcs", "tc_graph_create_csr", "tc_census", "tc_census_batch",
+                 "tc_graph_stats", "tc_graph_destroy", "tc_status_str"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", os.path.join(ROOT, "paper_1209_6308_gb300", "libtc.so")],
+                         capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (tc_[a-z0-9_]+)", out))
+    assert set(_declared_functions()) <= exported
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_1209_6308_gb300 as tc
+    assert set(_declared_functions()) <= set(tc.SIGNATURES)
+
+
+def test_library_table_matches_oracle_tables(lib):
+    import oracle
+    import paper_1209_6308_gb300 as tc
+    t = tc.tc_tricode_table()
+    assert (t == oracle.table_rules()).all()
+    assert (t == oracle.table_canonical()).all()
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 10, 1 << 20, (1 << 30)])
+def test_null_count_closed_form(lib, n):
+    import paper_1209_6308_gb300 as tc
+    c3 = n * (n - 1) * (n - 2) // 6 if n >= 3 else 0
+    assert tc.tc_null_count(n, [0] * 16) == c3
+    if c3 > 100:
+        counts = [0, 7, 5, 3] + [1] * 12
+        assert tc.tc_null_count(n, counts) == c3 - sum(counts[1:])
+
+
+def test_null_count_exceeds_64_bits(lib):
+    import paper_1209_6308_gb300 as tc
+    n = 1 << 26                       # C(2^26, 3) ~ 5e22 > 2^64
+    assert tc.tc_null_count(n, [0] * 16) == n * (n - 1) * (n - 2) // 6 > (1 << 64)
+
+
+def test_status_strings(lib):
+    import paper_1209_6308_gb300 as tc
+    for s, name in enumerate(["TC_OK", "TC_ERR_ARG", "TC_ERR_RANGE", "TC_ERR_OOM", "TC_ERR_CUDA",
+                              "TC_ERR_TIMEOUT", "TC_ERR_BUSY"]):
+        assert lib.tc_status_str(s).decode() == name
+
+
+def test_null_arguments_are_rejected_without_a_gpu(lib):
+    import paper_1209_6308_gb300 as tc
+    assert lib.tc_graph_create_arcs(4, 0, None, None, 0, None, None, None) == tc.TC_ERR_ARG
+    assert lib.tc_graph_stats(None, None) == tc.TC_ERR_ARG
+    out = ctypes.c_void_p()
+    assert lib.tc_graph_create_arcs(1 << 30 + 1, 0, None, None, 0, None, None, ctypes.byref(out)) == tc.TC_ERR_RANGE
+
+
+def test_struct_layouts_match_header(lib):
+    import paper_1209_6308_gb300 as tc
+    assert ctypes.sizeof(tc.tc_options) == 16 * 4
+    assert ctypes.sizeof(tc.tc_graph_info) == 8 + 8 * 8
+    assert ctypes.sizeof(tc.tc_u128) == 16

@@ -208,6 +208,18 @@ def test_sampled_timing_covers_the_whole_census_when_stride_is_one():
     assert ws == wt and part[1:] == full[1:] and sec >= 0
 
 
+def test_samples_partition_the_census():
+    """Samples over u = k (mod 5), k = 0..4, add up to the connected part of the census."""
+    n, s, d = graphgen.rmat(9, 16, 0.2, 3)
+    og = oracle.SampledGraph(n, s, d)
+    tot, work = [0] * 16, 0
+    for k in range(5):
+        _, part, ws, wt = og.sample(5, k)
+        tot = [a + b for a, b in zip(tot, part)]
+        work += ws
+    assert work == wt and tot[1:] == oracle.census_bm(n, s, d)[1:]
+
+
 def test_networkx_triadic_census_agrees():
     nx = pytest.importorskip("networkx")
     for (n, s, d) in (graphgen.rmat(8, 16, 0.15, 1), graphgen.gnp(50, 0.1, 2), graphgen.chung_lu(500, 8, 2.1, 0.1, 4, 3)):
