@@ -67,7 +67,8 @@ typedef struct {
     uint32_t algo;            /* tc_algo, default TC_ALGO_UNION */
     uint32_t schedule;        /* tc_schedule, default TC_SCHED_PLAIN */
     uint32_t warp_max_deg;    /* vertices u with deg <= this run one warp per u (default 64) */
-    uint32_t chunk_entries;   /* neighbour entries of u staged per CTA (default 4096, power of 2) */
+    uint32_t chunk_entries;   /* neighbour entries of u staged per CTA: power of 2 in [512, 16384],
+                                 at most 8192 for TC_ALGO_SUFFIX (default 4096) */
     uint32_t item_work;       /* target work per CTA item, in list entries touched (default 2^18) */
     uint32_t ctas_per_sm;     /* persistent CTAs per SM (default 3) */
     uint32_t reserved[10];
@@ -116,6 +117,19 @@ tc_status tc_census_opts(tc_graph* g, void* stream, const tc_options* opt, tc_u1
  * The null count needs 128-bit arithmetic: obtain it with tc_null_count.  Does not
  * synchronise; d_out16 must stay valid until the stream reaches the end of the census. */
 tc_status tc_census_async(tc_graph* g, void* stream, const tc_options* opt, uint64_t* d_out16);
+
+/* Instrumented census, for scheduling and for training the learned cost model: the same
+ * counts as tc_census_async into d_out16, plus the SM cycles spent on each vertex u (as the
+ * smaller endpoint of its pairs, Fig. 5 step 2) added into d_vcost[n] (device uint64, indexed
+ * by the relabelled id of tc_graph_device_csr; the caller zeroes it).  d_phase (device uint64,
+ * may be NULL) receives, for each of the tc_census_grid() CTAs, the global timer in ns at
+ * its start, at the end of its CTA work items and at its end.  Does not synchronise. */
+tc_status tc_census_profile(tc_graph* g, void* stream, const tc_options* opt, uint64_t* d_out16,
+                            uint64_t* d_vcost, uint64_t* d_phase);
+
+/* Number of CTAs the census launches on the current device for these options (opt may be
+ * NULL): the length / 3 of d_phase above. */
+uint32_t tc_census_grid(const tc_options* opt);
 
 /* Null count C(n,3) - sum(counts[1..15]) in 128-bit (Fig. 5 steps 3-5), on the host. */
 tc_u128 tc_null_count(uint32_t n, const uint64_t counts16[16]);

@@ -64,6 +64,8 @@ SIGNATURES = {
     "tc_census": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(tc_u128)]),
     "tc_census_opts": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(tc_u128)]),
     "tc_census_async": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "tc_census_profile": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "tc_census_grid": (ctypes.c_uint32, [_VP]),
     "tc_null_count": (tc_u128, [_U32, ctypes.POINTER(_U64)]),
     "tc_census_batch": (ctypes.c_int, [_VP, _U32, _VP, ctypes.POINTER(_U64), ctypes.POINTER(tc_u128)]),
     "tc_graph_stats": (ctypes.c_int, [_VP, ctypes.POINTER(tc_graph_info)]),
@@ -179,6 +181,25 @@ def tc_census_async(g: int, d_out16, stream=None, options=None) -> None:
         raise ValueError("d_out16 must be device memory")
     po, keepo = _options(options)
     _check(load().tc_census_async(g, _stream_handle(stream), po, p), "tc_census_async")
+
+
+def tc_census_profile(g: int, d_out16, d_vcost, d_phase=None, stream=None, options=None) -> None:
+    """Instrumented census: counts into d_out16, per-vertex SM cycles added into d_vcost[n]
+    (relabelled ids), optional per-CTA timestamps into d_phase[3 * tc_census_grid()]."""
+    p, dev, k1 = _buffer(d_out16, np.uint64)
+    pv, devv, k2 = _buffer(d_vcost, np.uint64)
+    pp = 0
+    if d_phase is not None:
+        pp, devp, k3 = _buffer(d_phase, np.uint64)
+    if not (dev and devv):
+        raise ValueError("d_out16 and d_vcost must be device memory")
+    po, keepo = _options(options)
+    _check(load().tc_census_profile(g, _stream_handle(stream), po, p, pv, pp or None), "tc_census_profile")
+
+
+def tc_census_grid(options=None) -> int:
+    po, keepo = _options(options)
+    return int(load().tc_census_grid(po))
 
 
 def tc_null_count(n: int, counts16) -> int:

@@ -79,7 +79,7 @@ int sm_count() {
     return c > 0 ? c : 1;
 }
 
-tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out) {
+Opts merge_opts(const tc_options* in, const Opts* base) {
     Opts o = base ? *base : Opts();
     if (in) {
         if (in->algo) o.algo = in->algo;
@@ -89,12 +89,21 @@ tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out) {
         if (in->item_work) o.item_work = in->item_work;
         if (in->ctas_per_sm) o.ctas_per_sm = in->ctas_per_sm;
     }
+    return o;
+}
+
+tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out) {
+    Opts o = merge_opts(in, base);
     if (o.algo > TC_ALGO_SUFFIX) return fail(TC_ERR_ARG, "unknown algo");
     if (o.schedule > TC_SCHED_LEARNED) return fail(TC_ERR_ARG, "unknown schedule");
-    if (o.chunk < 512 || o.chunk > 16384 || (o.chunk & (o.chunk - 1)))
-        return fail(TC_ERR_ARG, "chunk_entries must be a power of two in [512, 16384]");
+    if (!o.chunk) o.chunk = 4096;
+    if (!o.ctas_per_sm) o.ctas_per_sm = 3;
+    const uint32_t max_chunk = o.algo == TC_ALGO_SUFFIX ? 8192u : 16384u;   // shared-memory hash sizes
+    if (o.chunk < 512 || o.chunk > max_chunk || (o.chunk & (o.chunk - 1)))
+        return fail(TC_ERR_ARG, "chunk_entries must be a power of two in [512, 16384] (8192 for the suffix form)");
     if (o.warp_max_deg > o.chunk / 8) return fail(TC_ERR_ARG, "warp_max_deg must be <= chunk_entries / 8");
     if (o.ctas_per_sm < 1 || o.ctas_per_sm > 8) return fail(TC_ERR_ARG, "ctas_per_sm must be in [1, 8]");
+    if (o.item_work < 256) return fail(TC_ERR_ARG, "item_work must be >= 256");
     *out = o;
     return TC_OK;
 }
@@ -103,7 +112,9 @@ namespace {
 
 tc_status init_graph(tc_graph* g, uint32_t n, const tc_options* opt) {
     g->s.n = n;
-    TC_TRY(resolve_opts(opt, nullptr, &g->s.opts));
+    Opts check;
+    TC_TRY(resolve_opts(opt, nullptr, &check));
+    g->s.opts = merge_opts(opt, nullptr);
     TC_TRY(g->s.ctr.alloc_persistent(sizeof(uint32_t) * 4));
     TC_TRY(g->s.acc.alloc_persistent(sizeof(unsigned long long) * 16));
     TC_CUDA(cudaMallocHost(&g->s.h_counts, sizeof(unsigned long long) * 16));
@@ -292,6 +303,27 @@ tc_status tc_census_async(tc_graph* g, void* stream, const tc_options* opt, uint
     return census_enqueue(g->s, o, *p, st, reinterpret_cast<unsigned long long*>(d_out16));
 }
 
+tc_status tc_census_profile(tc_graph* g, void* stream, const tc_options* opt, uint64_t* d_out16, uint64_t* d_vcost,
+                            uint64_t* d_phase) {
+    if (!g || !d_out16 || !d_vcost) return fail(TC_ERR_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    Opts o;
+    TC_TRY(resolve_opts(opt, &g->s.opts, &o));
+    std::unique_lock<std::mutex> lk(g->s.busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(TC_ERR_BUSY, "graph is in use by another call");
+    Plan* p = nullptr;
+    TC_TRY(get_plan(g->s, o, st, &p));
+    TC_CUDA(cudaMemsetAsync(d_out16, 0, sizeof(uint64_t) * 16, st));
+    return census_enqueue(g->s, o, *p, st, reinterpret_cast<unsigned long long*>(d_out16),
+                          reinterpret_cast<unsigned long long*>(d_vcost), reinterpret_cast<unsigned long long*>(d_phase));
+}
+
+uint32_t tc_census_grid(const tc_options* opt) {
+    Opts o;
+    if (resolve_opts(opt, nullptr, &o) != TC_OK) return 0;
+    return (uint32_t)census_grid(o);
+}
+
 tc_status tc_census_opts(tc_graph* g, void* stream, const tc_options* opt, tc_u128 out[16]) {
     if (!g || !out) return fail(TC_ERR_ARG, "null argument");
     cudaStream_t st = (cudaStream_t)stream;
@@ -326,7 +358,8 @@ tc_status tc_census_batch(tc_graph* const* gs, uint32_t k, void* stream, uint64_
     TC_CUDA(cudaMemsetAsync(d.p, 0, sizeof(unsigned long long) * 16ull * k, st));
     for (uint32_t i = 0; i < k; ++i) {
         if (!gs[i]) return fail(TC_ERR_ARG, "null graph in batch");
-        Opts o = gs[i]->s.opts;
+        Opts o;
+        TC_TRY(resolve_opts(nullptr, &gs[i]->s.opts, &o));
         Plan* p = nullptr;
         TC_TRY(get_plan(gs[i]->s, o, st, &p));
         TC_TRY(census_enqueue(gs[i]->s, o, *p, st, d.as<unsigned long long>() + 16ull * i));

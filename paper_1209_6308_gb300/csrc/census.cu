@@ -22,10 +22,11 @@
 // atomics per CTA (the private census vectors of Sec. 6).
 //
 // Work decomposition ("manhattan collapse" of Sec. 7): vertices with deg > warp_max_deg
-// become CTA items (u, chunk of N[u] that fits in shared memory, range of v), sized by the
-// schedule; a hub's list is split into chunks and every chunk takes the part of each N[v]
-// that falls in its id range.  Vertices with smaller degree are handled one warp per vertex
-// after the items run out, in the same persistent launch.
+// become CTA items (u, range of pairs), sized by the schedule.  N[u] is staged one chunk at
+// a time; when a hub's list takes several chunks, each pair keeps a cursor into its sorted
+// N[v] and every chunk consumes the N[v] entries below the next chunk's first id, so each
+// N[v] entry is read once per pair with no search.  Vertices with smaller degree are
+// handled one warp per vertex after the items run out, in the same persistent launch.
 #include <atomic>
 
 #include "graph.cuh"
@@ -35,8 +36,15 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr uint32_t kEmpty = 0xffffffffu;
-constexpr uint32_t kFlushAfter = 1u << 26;   // list entries per CTA between histogram flushes
+constexpr uint32_t kEmpty = 0u;              // stored entries always have dir != 0
+#ifndef TC_UNROLL
+#define TC_UNROLL 4
+#endif
+#ifndef TC_MIN_BLOCKS
+#define TC_MIN_BLOCKS 3
+#endif
+constexpr int kUnroll = TC_UNROLL;           // v-side entries in flight per lane (per trip)
+constexpr uint32_t kTrip = 32u * TC_UNROLL;  // entries of N[v] per warp trip
 
 __device__ uint8_t d_tricode_class[64];
 
@@ -49,22 +57,19 @@ struct Params {
     uint32_t warp_max;
     uint32_t* ctr;                 // [0] next item, [1] next warp-tier vertex block
     unsigned long long* out;       // 16 accumulators
+    unsigned long long* vcost;     // optional [n]: SM cycles spent per vertex u (items summed)
+    unsigned long long* phase;     // optional [3 * gridDim]: globaltimer at start, end of items, end
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // tricode bits of the u-v link from dir(u,v) (bit 0 u->v, bit 1 v->u): 2 = u->v, 1 = v->u
 __device__ __forceinline__ uint32_t code_uv(uint32_t duv) { return ((duv & 1u) << 1) | (duv >> 1); }
 __device__ __forceinline__ uint32_t hash_slot(uint32_t x, int hb) { return (x * 2654435761u) >> (32 - hb); }
-
-// first index of a flagged ascending list whose id is >= val
-__device__ __forceinline__ uint32_t lower_bound_id(const uint32_t* a, uint32_t len, uint32_t val) {
-    const uint32_t key = val << 2;
-    uint32_t lo = 0, hi = len;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(a + mid) < key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
 
 __device__ __forceinline__ unsigned long long pack3(uint32_t c1, uint32_t c2, uint32_t c3) {
     return (unsigned long long)c1 | ((unsigned long long)c2 << 21) | ((unsigned long long)c3 << 42);
@@ -76,49 +81,178 @@ __device__ __forceinline__ unsigned long long ballot3(uint32_t e) {
                  __popc(__ballot_sync(0xffffffffu, e == 3u)));
 }
 
-__device__ __forceinline__ void hist_add(int* hist, uint32_t cls, int tid, int d) { hist[cls * kThreads + tid] += d; }
+// Per-lane counting state.
+//   racc   lane c < 16 holds the 64-bit total of class c.
+//   lo/hi  packed 8-bit counters per class (lo: classes 0-7, hi: 8-15) for triads classified one
+//          at a time (common neighbours past v, and the union walk's u-only triads), flushed
+//          into racc by a warp reduction before any byte can overflow.
+struct Counts {
+    unsigned long long lo, hi, racc;
+    uint32_t trips;   // warp-uniform: batches since the last flush, each adding <= kUnroll per byte
+};
 
-// Sum the per-thread histogram columns into the CTA's 64-bit accumulators and clear them.
-__device__ __forceinline__ void flush_hist(int* hist, unsigned long long* cacc, int warp, int lane) {
-    for (int cls = warp; cls < 16; cls += kWarps) {
-        long long s = 0;
+// Per-pair counts of one lane, 16-bit fields 1..3 keyed by a direction class d:
+//   vo[d]  third vertices w reached through v only, w > u, with dir(v,w) = d
+//   fo[d]  common neighbours w > v with dir(u,w) = d (their u-only count is taken back)
+//   cm     common neighbours (toward |N[u] n N[v]|)
+struct PairAcc {
+    unsigned long long vo, fo;
+    uint32_t cm, trips;
+};
+
+// A trip adds at most kUnroll to any packed byte or per-pair field of a lane.
+constexpr uint32_t kFlushTrips = 255u / kUnroll;             // packed 8-bit class counters
+constexpr uint32_t kPairSpillTrips = 65000u / kUnroll;       // per-pair 16-bit fields
+
+__device__ __forceinline__ void pk_add(Counts& k, uint32_t cls) {
+    const unsigned long long inc = 1ull << ((cls & 7u) << 3);
+    if (cls & 8u) k.hi += inc; else k.lo += inc;
+}
+
+__device__ __forceinline__ void pk_flush(Counts& k, int lane) {
 #pragma unroll
-        for (int q = 0; q < kThreads / 32; ++q) {
-            int i = cls * kThreads + lane + 32 * q;
-            s += hist[i];
-            hist[i] = 0;
-        }
+    for (int c = 0; c < 16; ++c) {
+        const unsigned long long pp = c < 8 ? k.lo : k.hi;
+        const uint32_t sum = __reduce_add_sync(0xffffffffu, (uint32_t)((pp >> ((c & 7) * 8)) & 255ull));
+        if (lane == c) k.racc += sum;
+    }
+    k.lo = k.hi = 0;
+    k.trips = 0;
+}
+
+__device__ __forceinline__ void pk_maybe_flush(Counts& k, int lane) {
+    if (k.trips >= kFlushTrips) pk_flush(k, lane);
+}
+
+// Fold one pair's per-lane counts into the class lanes.  suf holds the pair's u-only triads
+// per dir(u,w) class (packed 21-bit fields; 0 for the union walk, which counts them one by
+// one), dy the dyadic base n - d_u - d_v (0 after the pair's first chunk); the common
+// neighbours complete the dyadic count n - |S| - 2 (steps 2.1.2 - 2.1.3).
+__device__ __forceinline__ void pair_fold(Counts& k, PairAcc& pa, int lane, uint32_t duv, uint32_t cuv,
+                                          const uint8_t* sT, unsigned long long suf, unsigned long long dy) {
+    const uint32_t cm = __reduce_add_sync(0xffffffffu, pa.cm);
 #pragma unroll
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) cacc[cls] += (unsigned long long)s;
+    for (uint32_t d = 1; d <= 3; ++d) {
+        const uint32_t vs = __reduce_add_sync(0xffffffffu, (uint32_t)((pa.vo >> (16 * d)) & 0xffffull));
+        const uint32_t fs = __reduce_add_sync(0xffffffffu, (uint32_t)((pa.fo >> (16 * d)) & 0xffffull));
+        const int cv = sT[cuv | (d << 2)], cu = sT[cuv | (d << 4)];
+        if (lane == cv) k.racc += vs;
+        if (lane == cu) k.racc += ((suf >> (21 * (d - 1))) & 0x1fffffull) - (unsigned long long)fs;
+    }
+    if (lane == (duv == 3u ? 2 : 1)) k.racc += dy + cm;
+    pa.vo = pa.fo = 0;
+    pa.cm = 0;
+    pa.trips = 0;
+}
+
+// B entries [k0 + 32r + lane], cut at dv and, for a chunk with a successor, at hi_key
+template <bool HAS_HI>
+__device__ __forceinline__ void load_trip(uint32_t (&x)[kUnroll], const uint32_t* __restrict__ B, uint32_t k0,
+                                          uint32_t dv, uint32_t hi_key, int lane) {
+#pragma unroll
+    for (int r = 0; r < kUnroll; ++r) {
+        const uint32_t k = k0 + 32 * r + lane;
+        uint32_t e = k < dv ? __ldg(B + k) : 0u;
+        if (HAS_HI && e >= hi_key) e = 0u;
+        x[r] = e;
     }
 }
 
+// Classify one trip of N[v] entries (0 = no entry) against the staged hash of N[u]:
+//   found:  a common neighbour; counts toward |N[u] n N[v]| and, past v, is a triad with both
+//           links (its u-only count from the u side is taken back);
+//   else:   reached through v only; kept when w > u (the canonical rule of step 2.1.4).
+__device__ __forceinline__ void classify_trip(const uint32_t (&cur)[kUnroll], const uint32_t* sH, int hb,
+                                              uint32_t hmask, uint32_t u, uint32_t v, uint32_t cuv,
+                                              const uint8_t* sT, Counts& k, PairAcc& pa) {
+    uint32_t h[kUnroll], e[kUnroll];
+#pragma unroll
+    for (int r = 0; r < kUnroll; ++r) {
+        h[r] = hash_slot(cur[r] >> 2, hb);
+        e[r] = cur[r] ? sH[h[r]] : kEmpty;
+    }
+#pragma unroll
+    for (int r = 0; r < kUnroll; ++r) {
+        while (e[r] != kEmpty && (e[r] >> 2) != (cur[r] >> 2)) {
+            h[r] = (h[r] + 1) & hmask;
+            e[r] = sH[h[r]];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kUnroll; ++r) {
+        const uint32_t x = cur[r] >> 2, dvw = cur[r] & 3u;
+        if (e[r] != kEmpty) {
+            ++pa.cm;
+            if (x > v) {
+                const uint32_t duw = e[r] & 3u;
+                pk_add(k, sT[cuv | (dvw << 2) | (duw << 4)]);
+                pa.fo += 1ull << (duw << 4);
+            }
+        } else if (cur[r] && x > u) {
+            pa.vo += 1ull << (dvw << 4);
+        }
+    }
+    ++k.trips;
+    ++pa.trips;
+}
+
+// The v side of one pair (u, v) in a chunked hub: every w of N[v] from position k0 up to the
+// chunk's id bound is looked up in the staged hash of N[u].  Returns the position after the
+// last entry taken.
+__device__ __forceinline__ uint32_t v_side_chunk(const uint32_t* __restrict__ B, uint32_t k0, uint32_t dv,
+                                                 uint32_t hi_key, const uint32_t* sH, int hb, uint32_t hmask,
+                                                 uint32_t u, uint32_t v, uint32_t duv, uint32_t cuv, const uint8_t* sT,
+                                                 Counts& k, PairAcc& pa, int lane) {
+    uint32_t cur[kUnroll], nxt[kUnroll];
+    load_trip<true>(cur, B, k0, dv, hi_key, lane);
+    for (;;) {
+        pk_maybe_flush(k, lane);
+        if (pa.trips >= kPairSpillTrips) pair_fold(k, pa, lane, duv, cuv, sT, 0ull, 0ull);
+        load_trip<true>(nxt, B, k0 + kTrip, dv, hi_key, lane);
+        classify_trip(cur, sH, hb, hmask, u, v, cuv, sT, k, pa);
+        uint32_t taken = 0;
+#pragma unroll
+        for (int r = 0; r < kUnroll; ++r) taken += __popc(__ballot_sync(0xffffffffu, cur[r] != 0u));
+        k0 += taken;
+        if (taken < kTrip) break;
+#pragma unroll
+        for (int r = 0; r < kUnroll; ++r) cur[r] = nxt[r];
+    }
+    return k0;
+}
+
 template <int ALGO>
-__global__ void __launch_bounds__(kThreads, 3) k_census(Params P) {
+__global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t chunk = P.chunk;
-    uint32_t* sA = reinterpret_cast<uint32_t*>(smem);                       // [chunk]   staged N[u] chunk
-    uint32_t* sH = sA + chunk;                                               // [2*chunk] hash of the chunk
-    unsigned long long* sCk = reinterpret_cast<unsigned long long*>(sH + 2 * chunk);  // [chunk/32+1]
-    int* sHist = reinterpret_cast<int*>(sCk + chunk / 32 + 1);               // [16][kThreads]
-    unsigned long long* sW = reinterpret_cast<unsigned long long*>(sHist + 16 * kThreads);  // [kWarps][16]
-    unsigned long long* sC = sW + kWarps * 16;                               // [16]
-    uint8_t* sT = reinterpret_cast<uint8_t*>(sC + 16);                       // [64]
-    __shared__ uint32_t s_item, s_pending;
+    constexpr uint32_t kHashFactor = ALGO == TC_ALGO_UNION ? 2u : 4u;
+    // TC_ALGO_UNION keeps the sorted chunk for its walk; the suffix form needs the hash, the
+    // direction bit planes and their block prefix counts
+    uint32_t* sA = reinterpret_cast<uint32_t*>(smem);                                  // [chunk] (union)
+    uint32_t* sH = sA + (ALGO == TC_ALGO_UNION ? chunk : 0u);                          // [kHashFactor*chunk]
+    uint32_t* sLo = sH + kHashFactor * chunk;                                          // [chunk/32] dir bit 0
+    uint32_t* sHi = sLo + chunk / 32;                                                  // [chunk/32] dir bit 1
+    unsigned long long* sCk = reinterpret_cast<unsigned long long*>(sHi + chunk / 32); // [chunk/32+1]
+    uint32_t* sCur = reinterpret_cast<uint32_t*>(sCk + chunk / 32 + 1);               // [kMaxItemPairs]
+    unsigned long long* sC = reinterpret_cast<unsigned long long*>(sCur + kMaxItemPairs);  // [16]
+    uint8_t* sT = reinterpret_cast<uint8_t*>(sC + 16);                                // [64]
+    __shared__ uint32_t s_item, s_next;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < 16 * kThreads; i += kThreads) sHist[i] = 0;
-    if (tid < kWarps * 16) sW[tid] = 0;
     if (tid < 16) sC[tid] = 0;
     if (tid < 64) sT[tid] = d_tricode_class[tid];
-    if (tid == 0) s_pending = 0;
+    if (P.phase && tid == 0) P.phase[3 * blockIdx.x] = global_ns();
     __syncthreads();
 
     const uint64_t n = P.g.n;
     const uint64_t* __restrict__ off = P.g.off;
     const uint32_t* __restrict__ adj = P.g.adj;
-    unsigned long long* wacc = sW + warp * 16;
+    Counts cnt;
+    cnt.lo = cnt.hi = cnt.racc = 0;
+    cnt.trips = 0;
+    PairAcc pa;
+    pa.vo = pa.fo = 0;
+    pa.cm = pa.trips = 0;
 
     // ---------------------------------------------------------------- CTA items
     for (;;) {
@@ -127,183 +261,245 @@ __global__ void __launch_bounds__(kThreads, 3) k_census(Params P) {
         const uint32_t it = s_item;
         if (it >= P.n_items) break;
         const Item w = P.items[it];
+        const long long t_item = clock64();
         const uint32_t u = w.u;
         const uint64_t ubase = off[u];
         const uint32_t du = (uint32_t)(off[u + 1] - ubase);
-        const uint32_t LA = w.a1 - w.a0;
-        int hb = 6;
-        while ((1u << hb) < 2 * LA) ++hb;
-        const uint32_t H = 1u << hb;
-        for (uint32_t k = tid; k < LA; k += kThreads) sA[k] = adj[ubase + w.a0 + k];
-        for (uint32_t k = tid; k < H; k += kThreads) sH[k] = kEmpty;
-        __syncthreads();
-        for (uint32_t k = tid; k < LA; k += kThreads) {
-            const uint32_t e = sA[k];
-            uint32_t h = hash_slot(e >> 2, hb);
-            while (atomicCAS(&sH[h], kEmpty, e) != kEmpty) h = (h + 1) & (H - 1);
-        }
-        const uint32_t nq = (LA + 31) / 32;
-        if (ALGO == TC_ALGO_SUFFIX) {
+        const uint32_t nchunks = (du + chunk - 1) / chunk;
+        const uint32_t npairs = w.j1 - w.j0;                      // <= kMaxItemPairs
+        const uint32_t G = max(1u, min(32u, npairs / (4u * kWarps)));
+        if (nchunks > 1)
+            for (uint32_t i = tid; i < npairs; i += kThreads) sCur[i] = 0;
+
+        for (uint32_t c = 0; c < nchunks; ++c) {
+            const uint32_t a0 = c * chunk, a1 = min(du, a0 + chunk), LA = a1 - a0;
+            const uint32_t* __restrict__ Ach = adj + ubase + a0;
+            int hb = 6;
+            while ((1u << hb) < kHashFactor * LA) ++hb;
+            const uint32_t H = 1u << hb, hmask = H - 1;
+            for (uint32_t k = tid; k < H; k += kThreads) sH[k] = kEmpty;
+            if (tid == 0) s_next = 0;
+            __syncthreads();
+            // stage the chunk: hash (both forms), sorted copy (union), direction bit planes (suffix)
+            const uint32_t nq = (LA + 31) / 32;
             for (uint32_t q = warp; q < nq; q += kWarps) {
                 const uint32_t idx = q * 32 + lane;
-                const unsigned long long c = ballot3(idx < LA ? (sA[idx] & 3u) : 0u);
-                if (lane == 0) sCk[q + 1] = c;
+                const uint32_t e = idx < LA ? Ach[idx] : 0u;
+                if (idx < LA) {
+                    if (ALGO == TC_ALGO_UNION) sA[idx] = e;
+                    uint32_t h = hash_slot(e >> 2, hb);
+                    while (atomicCAS(&sH[h], kEmpty, e) != kEmpty) h = (h + 1) & hmask;
+                }
+                if (ALGO == TC_ALGO_SUFFIX) {
+                    const uint32_t bl = __ballot_sync(0xffffffffu, e & 1u), bh = __ballot_sync(0xffffffffu, e & 2u);
+                    if (lane == 0) {
+                        sLo[q] = bl;
+                        sHi[q] = bh;
+                        sCk[q + 1] = pack3(__popc(bl & ~bh), __popc(bh & ~bl), __popc(bl & bh));
+                    }
+                }
             }
             __syncthreads();
-            if (warp == 0) {   // inclusive scan of the block counts -> prefix before each block
-                unsigned long long carry = 0;
-                for (uint32_t b = 0; b < nq; b += 32) {
-                    unsigned long long x = (b + lane < nq) ? sCk[b + lane + 1] : 0ull;
+            if (ALGO == TC_ALGO_SUFFIX) {
+                if (warp == 0) {   // inclusive scan of the block counts -> counts before each block
+                    unsigned long long carry = 0;
+                    for (uint32_t b = 0; b < nq; b += 32) {
+                        unsigned long long x = (b + lane < nq) ? sCk[b + lane + 1] : 0ull;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-                        if (lane >= o) x += y;
+                        for (int o = 1; o < 32; o <<= 1) {
+                            unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+                            if (lane >= o) x += y;
+                        }
+                        if (b + lane < nq) sCk[b + lane + 1] = x + carry;
+                        carry += __shfl_sync(0xffffffffu, x, 31);
                     }
-                    if (b + lane < nq) sCk[b + lane + 1] = x + carry;
-                    carry += __shfl_sync(0xffffffffu, x, 31);
+                    if (lane == 0) sCk[0] = 0;
                 }
-                if (lane == 0) sCk[0] = 0;
+                __syncthreads();
             }
-        }
-        __syncthreads();
 
-        const uint32_t lo_val = w.a0 ? (sA[0] >> 2) : 0u;
-        const bool has_hi = w.a1 < du;
-        const uint32_t hi_val = has_hi ? (adj[ubase + w.a1] >> 2) : 0u;
-        uint32_t pend = 0;
-        for (uint32_t j = w.j0 + warp; j < w.j1; j += kWarps) {
-            const uint32_t euv = adj[ubase + j];
-            const uint32_t v = euv >> 2, duv = euv & 3u, cuv = code_uv(duv);
-            const uint64_t vb = off[v];
-            const uint32_t dv = (uint32_t)(off[v + 1] - vb);
-            const uint32_t* __restrict__ B = adj + vb;
-            const uint32_t b0 = w.a0 ? lower_bound_id(B, dv, lo_val) : 0u;
-            const uint32_t b1 = has_hi ? lower_bound_id(B, dv, hi_val) : dv;
-            uint32_t c = 0;
-            for (uint32_t k = b0 + lane; k < b1; k += 32) {       // v side
-                const uint32_t xe = B[k], x = xe >> 2, dvw = xe & 3u;
-                uint32_t h = hash_slot(x, hb), e;
-                bool found = false;
-                while ((e = sH[h]) != kEmpty) {
-                    if ((e >> 2) == x) { found = true; break; }
-                    h = (h + 1) & (H - 1);
-                }
-                if (found) {
-                    ++c;
-                    if (x > v) {
-                        const uint32_t duw = e & 3u;
-                        hist_add(sHist, sT[cuv | (dvw << 2) | (duw << 4)], tid, 1);
-                        hist_add(sHist, sT[cuv | (duw << 4)], tid, -1);
+            // N[v] entries with id >= the next chunk's first id belong to later chunks
+            const bool has_hi = a1 < du;
+            const uint32_t hi_key = has_hi ? (adj[ubase + a1] & ~3u) : 0u;
+            for (;;) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(&s_next, G);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (base >= npairs) break;
+                // prefetch the grabbed pairs: lane l holds pair base + l
+                const uint32_t np = min(G, npairs - base);
+                const bool okl = (uint32_t)lane < np;
+                const uint32_t euv_l = okl ? adj[ubase + w.j0 + base + lane] : 0u;
+                const uint64_t vb_l = okl ? off[euv_l >> 2] : 0ull;
+                const uint32_t dv_l = okl ? (uint32_t)(off[(euv_l >> 2) + 1] - vb_l) : 0u;
+                const uint32_t cur_l = (okl && nchunks > 1) ? sCur[base + lane] : 0u;
+                // u side of pair t of this grab and the fold of its counts
+                auto finish_pair = [&](uint32_t t, uint32_t duv, uint32_t cuv, uint32_t dv) {
+                    const uint32_t j = w.j0 + base + t;
+                    uint32_t s0 = (j + 1 > a0 ? j + 1 : a0) - a0;        // chunk entries past v
+                    if (s0 > LA) s0 = LA;
+                    unsigned long long suf = 0;
+                    if (ALGO == TC_ALGO_UNION) {
+                        for (uint32_t kb = s0; kb < LA; kb += 32) {
+                            pk_maybe_flush(cnt, lane);
+                            const uint32_t k = kb + lane;
+                            if (k < LA) pk_add(cnt, sT[cuv | ((sA[k] & 3u) << 4)]);
+                            ++cnt.trips;
+                        }
+                    } else {
+                        const uint32_t q = s0 >> 5, r = s0 & 31u;
+                        const uint32_t m = (1u << r) - 1u;
+                        const uint32_t bl = r ? (sLo[q] & m) : 0u, bh = r ? (sHi[q] & m) : 0u;
+                        suf = sCk[nq] - sCk[q] - pack3(__popc(bl & ~bh), __popc(bh & ~bl), __popc(bl & bh));
                     }
-                } else if (x > u) {
-                    hist_add(sHist, sT[cuv | (dvw << 2)], tid, 1);
-                }
-            }
-            c = __reduce_add_sync(0xffffffffu, c);
-            uint32_t s0 = (j + 1 > w.a0 ? j + 1 : w.a0) - w.a0;   // u side: chunk entries past v
-            if (s0 > LA) s0 = LA;
-            if (ALGO == TC_ALGO_UNION) {
-                for (uint32_t k = s0 + lane; k < LA; k += 32) hist_add(sHist, sT[cuv | ((sA[k] & 3u) << 4)], tid, 1);
-            } else {
-                const uint32_t q = s0 >> 5, r = s0 & 31u, idx = q * 32 + lane;
-                const unsigned long long part = ballot3((lane < r && idx < LA) ? (sA[idx] & 3u) : 0u);
-                const unsigned long long suf = sCk[nq] - sCk[q] - part;
-                if (lane == 0) {
+                    pair_fold(cnt, pa, lane, duv, cuv, sT, suf, c == 0 ? n - du - dv : 0ull);
+                };
+                if (has_hi) {
+                    // chunked hub: each pair resumes at its cursor and stops at the chunk's id bound
+                    for (uint32_t t = 0; t < np; ++t) {
+                        const uint32_t euv = __shfl_sync(0xffffffffu, euv_l, t);
+                        const uint64_t vb = __shfl_sync(0xffffffffu, vb_l, t);
+                        const uint32_t dv = __shfl_sync(0xffffffffu, dv_l, t);
+                        const uint32_t start = __shfl_sync(0xffffffffu, cur_l, t);
+                        const uint32_t v = euv >> 2, duv = euv & 3u, cuv = code_uv(duv);
+                        const uint32_t kend =
+                            v_side_chunk(adj + vb, start, dv, hi_key, sH, hb, hmask, u, v, duv, cuv, sT, cnt, pa, lane);
+                        if (lane == 0) sCur[base + t] = kend;
+                        finish_pair(t, duv, cuv, dv);
+                    }
+                } else {
+                    // the rest of each N[v]: one flattened (pair, trip) loop whose next trip's
+                    // loads, possibly of the next pair, are in flight while this one is classified
+                    uint32_t t = 0, k0 = nchunks > 1 ? __shfl_sync(0xffffffffu, cur_l, 0) : 0u;
+                    uint32_t euv = __shfl_sync(0xffffffffu, euv_l, 0);
+                    uint64_t vb = __shfl_sync(0xffffffffu, vb_l, 0);
+                    uint32_t dv = __shfl_sync(0xffffffffu, dv_l, 0);
+                    uint32_t cur[kUnroll], nxt[kUnroll];
+                    load_trip<false>(cur, adj + vb, k0, dv, 0u, lane);
+                    for (;;) {
+                        pk_maybe_flush(cnt, lane);
+                        const uint32_t v = euv >> 2, duv = euv & 3u, cuv = code_uv(duv);
+                        if (pa.trips >= kPairSpillTrips) pair_fold(cnt, pa, lane, duv, cuv, sT, 0ull, 0ull);
+                        uint32_t nt = t, nk0 = k0 + kTrip;
+                        if (nk0 >= dv) {
+                            nt = t + 1;
+                            nk0 = (nchunks > 1 && nt < np) ? __shfl_sync(0xffffffffu, cur_l, nt) : 0u;
+                        }
+                        const bool more = nt < np;
+                        uint32_t neuv = euv, ndv = dv;
+                        uint64_t nvb = vb;
+                        if (nt != t && more) {
+                            neuv = __shfl_sync(0xffffffffu, euv_l, nt);
+                            nvb = __shfl_sync(0xffffffffu, vb_l, nt);
+                            ndv = __shfl_sync(0xffffffffu, dv_l, nt);
+                        }
+                        if (more) load_trip<false>(nxt, adj + nvb, nk0, ndv, 0u, lane);
+                        classify_trip(cur, sH, hb, hmask, u, v, cuv, sT, cnt, pa);
+                        if (nt != t) {
+                            if (nchunks > 1 && lane == 0) sCur[base + t] = dv;
+                            finish_pair(t, duv, cuv, dv);
+                        }
+                        if (!more) break;
+                        t = nt;
+                        k0 = nk0;
+                        euv = neuv;
+                        vb = nvb;
+                        dv = ndv;
 #pragma unroll
-                    for (uint32_t d = 1; d <= 3; ++d) {
-                        const unsigned long long cnt = (suf >> (21 * (d - 1))) & 0x1fffffull;
-                        if (cnt) wacc[sT[cuv | (d << 4)]] += cnt;
+                        for (int r = 0; r < kUnroll; ++r) cur[r] = nxt[r];
                     }
                 }
             }
-            if (lane == 0) {
-                const unsigned long long dy = (w.a0 == 0 ? n - du - dv : 0ull) + c;
-                wacc[duv == 3u ? 2 : 1] += dy;
-                pend += (b1 - b0) + (ALGO == TC_ALGO_UNION ? LA - s0 : 0u);
-            }
+            __syncthreads();   // all warps are done with this chunk before it is replaced
         }
-        if (lane == 0) atomicAdd(&s_pending, pend);
-        __syncthreads();
-        if (s_pending > kFlushAfter) {
-            flush_hist(sHist, sC, warp, lane);
-            __syncthreads();
-            if (tid == 0) s_pending = 0;
-        }
+        if (P.vcost && tid == 0) atomicAdd(&P.vcost[u], (unsigned long long)(clock64() - t_item));
     }
+    if (P.phase && tid == 0) P.phase[3 * blockIdx.x + 1] = global_ns();
 
     // ---------------------------------------------------------------- one warp per vertex
-    uint32_t* wA = sA + warp * P.warp_max;
+    uint32_t* wA = reinterpret_cast<uint32_t*>(smem) + warp * P.warp_max;
     for (;;) {
         uint32_t ub = 0;
         if (lane == 0) ub = atomicAdd(&P.ctr[1], 32u);
         ub = __shfl_sync(0xffffffffu, ub, 0);
+        if (ub >= P.warp_end - P.warp_begin) break;
         const uint32_t u0 = P.warp_begin + ub;
-        if (u0 >= P.warp_end || ub >= P.warp_end) break;
         const uint32_t u1 = min(u0 + 32u, P.warp_end);
         for (uint32_t u = u0; u < u1; ++u) {
             const uint64_t ubase = off[u];
             const uint32_t du = (uint32_t)(off[u + 1] - ubase);
             const uint32_t p0 = P.g.up[u];
             if (p0 >= du) continue;
+            const long long t_vert = clock64();
             __syncwarp();
             for (uint32_t k = lane; k < du; k += 32) wA[k] = adj[ubase + k];
             __syncwarp();
-            for (uint32_t j = p0; j < du; ++j) {
-                const uint32_t euv = wA[j];
-                const uint32_t v = euv >> 2, duv = euv & 3u, cuv = code_uv(duv);
-                const uint64_t vb = off[v];
-                const uint32_t dv = (uint32_t)(off[v + 1] - vb);
-                const uint32_t* __restrict__ B = adj + vb;
-                uint32_t c = 0;
-                for (uint32_t k = lane; k < dv; k += 32) {
-                    const uint32_t xe = B[k], x = xe >> 2, dvw = xe & 3u;
-                    uint32_t lo = 0, hi = du;
-                    while (lo < hi) {
-                        uint32_t mid = (lo + hi) >> 1;
-                        if ((wA[mid] >> 2) < x) lo = mid + 1; else hi = mid;
-                    }
-                    if (lo < du && (wA[lo] >> 2) == x) {
-                        ++c;
-                        if (x > v) {
-                            const uint32_t duw = wA[lo] & 3u;
-                            hist_add(sHist, sT[cuv | (dvw << 2) | (duw << 4)], tid, 1);
-                            hist_add(sHist, sT[cuv | (duw << 4)], tid, -1);
+            for (uint32_t jb = p0; jb < du; jb += 32) {
+                const uint32_t jl = jb + lane;
+                const bool okl = jl < du;
+                const uint32_t euv_l = okl ? wA[jl] : 0u;
+                const uint64_t vb_l = okl ? off[euv_l >> 2] : 0ull;
+                const uint32_t dv_l = okl ? (uint32_t)(off[(euv_l >> 2) + 1] - vb_l) : 0u;
+                const uint32_t np = min(32u, du - jb);
+                for (uint32_t t = 0; t < np; ++t) {
+                    const uint32_t euv = __shfl_sync(0xffffffffu, euv_l, t);
+                    const uint64_t vb = __shfl_sync(0xffffffffu, vb_l, t);
+                    const uint32_t dv = __shfl_sync(0xffffffffu, dv_l, t);
+                    const uint32_t v = euv >> 2, duv = euv & 3u, cuv = code_uv(duv);
+                    const uint32_t* __restrict__ B = adj + vb;
+                    const uint32_t j = jb + t;
+                    for (uint32_t kb = 0; kb < dv; kb += 32) {
+                        pk_maybe_flush(cnt, lane);
+                        if (pa.trips >= kPairSpillTrips) pair_fold(cnt, pa, lane, duv, cuv, sT, 0ull, 0ull);
+                        const uint32_t k = kb + lane;
+                        if (k < dv) {
+                            const uint32_t xe = __ldg(B + k), x = xe >> 2, dvw = xe & 3u;
+                            uint32_t lo = 0, hi = du;
+                            while (lo < hi) {
+                                const uint32_t mid = (lo + hi) >> 1;
+                                if ((wA[mid] >> 2) < x) lo = mid + 1; else hi = mid;
+                            }
+                            if (lo < du && (wA[lo] >> 2) == x) {
+                                ++pa.cm;
+                                if (x > v) {
+                                    const uint32_t duw = wA[lo] & 3u;
+                                    pk_add(cnt, sT[cuv | (dvw << 2) | (duw << 4)]);
+                                    pa.fo += 1ull << (duw << 4);
+                                }
+                            } else if (x > u) {
+                                pa.vo += 1ull << (dvw << 4);
+                            }
                         }
-                    } else if (x > u) {
-                        hist_add(sHist, sT[cuv | (dvw << 2)], tid, 1);
+                        ++cnt.trips;
+                        ++pa.trips;
                     }
-                }
-                c = __reduce_add_sync(0xffffffffu, c);
-                if (ALGO == TC_ALGO_UNION) {
-                    for (uint32_t k = j + 1 + lane; k < du; k += 32) hist_add(sHist, sT[cuv | ((wA[k] & 3u) << 4)], tid, 1);
-                } else {
                     unsigned long long suf = 0;
-                    for (uint32_t b = (j + 1) & ~31u; b < du; b += 32) {
-                        const uint32_t k = b + lane;
-                        suf += ballot3((k > j && k < du) ? (wA[k] & 3u) : 0u);
-                    }
-                    if (lane == 0) {
-#pragma unroll
-                        for (uint32_t d = 1; d <= 3; ++d) {
-                            const unsigned long long cnt = (suf >> (21 * (d - 1))) & 0x1fffffull;
-                            if (cnt) wacc[sT[cuv | (d << 4)]] += cnt;
+                    if (ALGO == TC_ALGO_UNION) {
+                        for (uint32_t kb = j + 1; kb < du; kb += 32) {
+                            pk_maybe_flush(cnt, lane);
+                            const uint32_t k = kb + lane;
+                            if (k < du) pk_add(cnt, sT[cuv | ((wA[k] & 3u) << 4)]);
+                            ++cnt.trips;
+                        }
+                    } else {
+                        for (uint32_t b = (j + 1) & ~31u; b < du; b += 32) {
+                            const uint32_t k = b + lane;
+                            suf += ballot3((k > j && k < du) ? (wA[k] & 3u) : 0u);
                         }
                     }
+                    pair_fold(cnt, pa, lane, duv, cuv, sT, suf, n - du - dv);
                 }
-                if (lane == 0) wacc[duv == 3u ? 2 : 1] += (n - du - dv) + c;
             }
+            if (P.vcost && lane == 0) P.vcost[u] += (unsigned long long)(clock64() - t_vert);
         }
     }
 
+    // ---------------------------------------------------------------- totals
+    pk_flush(cnt, lane);
+    if (lane < 16 && cnt.racc) atomicAdd(&sC[lane], cnt.racc);
     __syncthreads();
-    flush_hist(sHist, sC, warp, lane);
-    __syncthreads();
-    if (tid < 16) {
-        unsigned long long t = sC[tid];
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) t += sW[w * 16 + tid];
-        if (t) atomicAdd(&P.out[tid], t);
-    }
+    if (tid < 16 && sC[tid]) atomicAdd(&P.out[tid], sC[tid]);
+    if (P.phase && tid == 0) P.phase[3 * blockIdx.x + 2] = global_ns();
 }
 
 // ---------------------------------------------------------------- schedule (plan) kernels
@@ -315,47 +511,43 @@ __global__ void k_count_gt(const uint64_t* off, uint32_t n, uint32_t thr, uint32
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
 }
 
-// Items per vertex u < u_end: C chunks of N[u] times S ranges of v, with S from the
-// estimated work of u's pairs (degrees for the plain schedule, the cost model if given).
+// Items per vertex u < u_end: S ranges of u's pairs, S from the estimated work of u's
+// pairs (degrees for the plain schedule, the cost model if given) and at most
+// kMaxItemPairs pairs per item.
 __global__ void k_plan_count(GraphDev g, uint32_t u_end, uint32_t chunk, uint32_t item_work, int algo, float dbar,
-                             const float* cost, uint32_t* cnt, uint32_t* split) {
+                             const float* cost, uint32_t* cnt) {
     for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < u_end; x += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t du = (uint32_t)(g.off[x + 1] - g.off[x]);
         const uint32_t P = du - g.up[x];
-        if (P == 0) { cnt[x] = 0; split[x] = 0; continue; }
+        if (P == 0) { cnt[x] = 0; continue; }
         const uint32_t C = (du + chunk - 1) / chunk;
         double est;
         if (cost) est = (double)cost[x];
-        else est = (double)P * ((double)dbar + 16.0) + (algo == TC_ALGO_UNION ? 0.5 * (double)P * (double)du : 0.0);
-        double s = ceil(est / (double)C / (double)item_work);
+        else est = (double)P * ((double)dbar + 16.0 + 16.0 * (double)C) +
+                   (algo == TC_ALGO_UNION ? 0.5 * (double)P * (double)du : 0.0);
+        double s = ceil(est / (double)item_work);
+        const double smin = ceil((double)P / (double)kMaxItemPairs);
+        if (s < smin) s = smin;
         if (s < 1.0) s = 1.0;
         if (s > (double)P) s = (double)P;
-        const uint32_t S = (uint32_t)s;
-        cnt[x] = C * S;
-        split[x] = S;
+        cnt[x] = (uint32_t)s;
     }
 }
 
-__global__ void k_plan_emit(GraphDev g, uint32_t u_end, uint32_t chunk, const uint32_t* pos, const uint32_t* split,
-                            Item* items) {
+__global__ void k_plan_emit(GraphDev g, uint32_t u_end, const uint32_t* pos, const uint32_t* cnt, Item* items) {
     for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < u_end; x += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t S = split[x];
+        const uint32_t S = cnt[x];
         if (!S) continue;
         const uint32_t du = (uint32_t)(g.off[x + 1] - g.off[x]);
         const uint32_t up = g.up[x], P = du - up;
-        const uint32_t C = (du + chunk - 1) / chunk;
         uint32_t o = pos[x];
-        for (uint32_t c = 0; c < C; ++c) {
-            const uint32_t a0 = c * chunk, a1 = min(du, a0 + chunk);
-            for (uint32_t s = 0; s < S; ++s) {
-                Item it;
-                it.u = (uint32_t)x;
-                it.a0 = a0;
-                it.a1 = a1;
-                it.j0 = up + (uint32_t)((uint64_t)P * s / S);
-                it.j1 = up + (uint32_t)((uint64_t)P * (s + 1) / S);
-                items[o++] = it;
-            }
+        for (uint32_t s = 0; s < S; ++s) {
+            Item it;
+            it.u = (uint32_t)x;
+            it.j0 = up + (uint32_t)((uint64_t)P * s / S);
+            it.j1 = up + (uint32_t)((uint64_t)P * (s + 1) / S);
+            it.pad = 0;
+            items[o++] = it;
         }
     }
 }
@@ -363,9 +555,10 @@ __global__ void k_plan_emit(GraphDev g, uint32_t u_end, uint32_t chunk, const ui
 std::atomic<uint64_t> g_table_uploaded{0};
 std::atomic<uint64_t> g_attr_set[2] = {{0}, {0}};
 
-size_t census_smem(uint32_t chunk) {
-    return sizeof(uint32_t) * 3ull * chunk + sizeof(unsigned long long) * (chunk / 32 + 1) +
-           sizeof(int) * 16ull * kThreads + sizeof(unsigned long long) * (kWarps * 16 + 16) + 64;
+size_t census_smem(uint32_t algo, uint32_t chunk) {
+    return sizeof(uint32_t) * (algo == TC_ALGO_UNION ? 3ull : 4ull) * chunk + sizeof(uint32_t) * (chunk / 16) +
+           sizeof(unsigned long long) * (chunk / 32 + 1) + sizeof(uint32_t) * kMaxItemPairs +
+           sizeof(unsigned long long) * 16 + 64;
 }
 
 tc_status prepare_device(cudaStream_t st, int algo, size_t smem) {
@@ -396,6 +589,8 @@ tc_status prepare_device(cudaStream_t st, int algo, size_t smem) {
 tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out) {
     for (auto& p : g.plans)
         if (p.valid && p.key == o) { *out = &p; return TC_OK; }
+    if (o.schedule == TC_SCHED_LEARNED && !g.cost.p)
+        return fail(TC_ERR_ARG, "learned schedule requested but no cost model is attached");
     Plan& p = g.plans[g.next_plan];
     g.next_plan = (g.next_plan + 1) % GraphStore::kPlans;
     p.valid = false;
@@ -414,24 +609,22 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out) {
     p.warp_end = g.n_active;
     p.n_items = 0;
     if (u_end) {
-        DevBuf cnt, split, pos, tot;
+        DevBuf cnt, pos, tot;
         TC_TRY(cnt.alloc(sizeof(uint32_t) * u_end, st));
-        TC_TRY(split.alloc(sizeof(uint32_t) * u_end, st));
         TC_TRY(pos.alloc(sizeof(uint32_t) * u_end, st));
         TC_TRY(tot.alloc(sizeof(uint32_t), st));
         const float dbar = g.n_active ? (float)(2.0 * (double)g.e_sym / (double)g.n_active) : 0.f;
         const float* cost = (o.schedule == TC_SCHED_LEARNED) ? g.cost.as<float>() : nullptr;
-        if (o.schedule == TC_SCHED_LEARNED && !cost) return fail(TC_ERR_ARG, "learned schedule requested but no cost model is attached");
         k_plan_count<<<grid_for(u_end, 256, 4096), 256, 0, st>>>(gd, u_end, o.chunk, o.item_work, (int)o.algo, dbar, cost,
-                                                                  cnt.as<uint32_t>(), split.as<uint32_t>());
+                                                                  cnt.as<uint32_t>());
         TC_LAUNCH("k_plan_count");
         TC_TRY(scan_u32(cnt.as<uint32_t>(), pos.as<uint32_t>(), u_end, tot.as<uint32_t>(), st));
         TC_CUDA(cudaMemcpyAsync(&p.n_items, tot.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
         TC_TRY(p.items.alloc_persistent(sizeof(Item) * (p.n_items ? p.n_items : 1)));
         if (p.n_items) {
-            k_plan_emit<<<grid_for(u_end, 256, 4096), 256, 0, st>>>(gd, u_end, o.chunk, pos.as<uint32_t>(),
-                                                                     split.as<uint32_t>(), p.items.as<Item>());
+            k_plan_emit<<<grid_for(u_end, 256, 4096), 256, 0, st>>>(gd, u_end, pos.as<uint32_t>(), cnt.as<uint32_t>(),
+                                                                     p.items.as<Item>());
             TC_LAUNCH("k_plan_emit");
         }
         TC_CUDA(cudaStreamSynchronize(st));
@@ -441,9 +634,12 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out) {
     return TC_OK;
 }
 
-tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16) {
+int census_grid(const Opts& o) { return sm_count() * (int)o.ctas_per_sm; }
+
+tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16,
+                         unsigned long long* d_vcost, unsigned long long* d_phase) {
     if (g.e_sym == 0) return TC_OK;
-    const size_t smem = census_smem(o.chunk);
+    const size_t smem = census_smem(o.algo, o.chunk);
     TC_TRY(prepare_device(st, (int)o.algo, smem));
     TC_CUDA(cudaMemsetAsync(g.ctr.p, 0, sizeof(uint32_t) * 4, st));
     Params P;
@@ -456,7 +652,9 @@ tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream
     P.warp_max = o.warp_max_deg;
     P.ctr = g.ctr.as<uint32_t>();
     P.out = d_out16;
-    const unsigned grid = (unsigned)(sm_count() * (int)o.ctas_per_sm);
+    P.vcost = d_vcost;
+    P.phase = d_phase;
+    const unsigned grid = (unsigned)census_grid(o);
     if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION><<<grid, kThreads, smem, st>>>(P);
     else k_census<TC_ALGO_SUFFIX><<<grid, kThreads, smem, st>>>(P);
     TC_LAUNCH("k_census");

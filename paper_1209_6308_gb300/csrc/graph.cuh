@@ -8,21 +8,26 @@
 
 namespace tc {
 
-// Resolved census options (defaults filled in).
+// Census options.  chunk and ctas_per_sm may be 0 (= automatic) until finalised for the
+// chosen kernel family: the suffix form keeps only a hash in shared memory, so it takes
+// twice the chunk at two CTAs per SM; the union walk also keeps the sorted chunk.
 struct Opts {
     uint32_t algo = TC_ALGO_UNION;
     uint32_t schedule = TC_SCHED_PLAIN;
     uint32_t warp_max_deg = 64;
-    uint32_t chunk = 4096;
+    uint32_t chunk = 0;
     uint32_t item_work = 1u << 18;
-    uint32_t ctas_per_sm = 3;
+    uint32_t ctas_per_sm = 0;
     bool operator==(const Opts& o) const {
         return algo == o.algo && schedule == o.schedule && warp_max_deg == o.warp_max_deg && chunk == o.chunk &&
                item_work == o.item_work && ctas_per_sm == o.ctas_per_sm;
     }
 };
 
+// Overlay the non-zero fields of `in` on `base`, fill the automatic values and validate.
 tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out);
+// Overlay only (automatic values kept), for a graph's stored defaults.
+Opts merge_opts(const tc_options* in, const Opts* base);
 
 // A census plan: the CTA work items for the vertices with deg > warp_max_deg, and the
 // id range of the vertices handled one warp per vertex.
@@ -66,7 +71,11 @@ tc_status build_from_csr(GraphStore& g, const uint64_t* d_off, const uint32_t* d
 // caller zeroes; index 0 is never touched).  No host synchronisation, no allocation once
 // the plan for `o` exists (get_plan allocates it on first use).
 tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out);
-tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16);
+// d_vcost (optional, [n] uint64, caller-zeroed) receives the SM cycles spent per vertex u;
+// d_phase (optional, [3 * CTAs] uint64) the globaltimer at start, end of items, end per CTA.
+tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16,
+                         unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr);
+int census_grid(const Opts& o);
 
 // The library's tricode -> class table (derived in tables.cu); census.cu copies it into
 // its device memory before the first census.

@@ -60,11 +60,12 @@ struct GraphDev {
     const uint32_t* up;     // [n] number of neighbours with a smaller id (index of first v > u)
 };
 
-// One CTA work item of the census: vertex u, the chunk [a0, a1) of N[u] staged in shared
-// memory, and the pairs (u, N[u][j]) for j in [j0, j1) (all with N[u][j] > u).
+// One CTA work item of the census: vertex u and its pairs (u, N[u][j]) for j in [j0, j1)
+// (all with N[u][j] > u).  N[u] is staged in shared memory one chunk at a time.
 struct Item {
-    uint32_t u, a0, a1, j0, j1;
+    uint32_t u, j0, j1, pad;
 };
+constexpr uint32_t kMaxItemPairs = 1024;   // pairs per item (one N[v] cursor each in shared memory)
 
 // ------------------------------------------------------------------ primitives
 // Exclusive scan of n uint32 values into uint32 (out may alias nothing); *total (device

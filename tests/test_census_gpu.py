@@ -17,7 +17,7 @@ ALGOS = [{"algo": 0}, {"algo": 1}]
 TIERS = [
     {},                                                       # defaults: warp <= 64, chunk 4096
     {"warp_max_deg": 8, "chunk_entries": 512, "item_work": 2048},   # tiny chunks: hubs split
-    {"warp_max_deg": 64, "chunk_entries": 16384, "item_work": 1 << 22, "ctas_per_sm": 1},
+    {"warp_max_deg": 64, "chunk_entries": 8192, "item_work": 1 << 22, "ctas_per_sm": 1},
 ]
 
 
