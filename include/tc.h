@@ -156,6 +156,24 @@ void tc_graph_destroy(tc_graph* g);
 const char* tc_status_str(tc_status s);
 const char* tc_last_error(void);
 
+/* Census that allocates nothing, for callers that cannot call cudaMalloc (allocation is
+ * forbidden or must not block where they run, or all device memory is already reserved by
+ * their own pool).  The paper has no counterpart to this entry point.
+ *
+ * Input: a device CSR in this library's form, as tc_graph_device_csr returns it: d_off[n+1]
+ * (uint64) and d_adj (uint32 (id << 2) | dir, ascending per list, symmetric), with vertex
+ * degrees not increasing with the id.  Output: d_out16 (device, 16 uint64) as for
+ * tc_census_async (index 0 = 0; get the null count with tc_null_count).
+ * Scratch: one fixed 8 MiB device array inside the library, so n <= 2^20 (larger n gives
+ * TC_ERR_RANGE, as does a graph needing more than 2^18 work items); lists out of degree order
+ * give TC_ERR_ARG.  Every GPU that loads the library holds the array until the process exits.
+ * The first call on a device looks up the array's device address; make that first call
+ * before any stream capture.  All calls share the array and it keeps the last call's
+ * contents, so calls that overlap on the GPU race: serialise them.  The call synchronises
+ * `stream` while it sizes the work, then enqueues the census and returns. */
+tc_status tc_census_csr_noalloc(uint32_t n, const uint64_t* d_off, const uint32_t* d_adj, void* stream,
+                                uint64_t* d_out16);
+
 /* The 64-entry tricode -> class table the kernels use (for inspection and tests). */
 void tc_tricode_table(uint8_t out[64]);
 

@@ -66,6 +66,7 @@ SIGNATURES = {
     "tc_census_async": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "tc_census_profile": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "tc_census_grid": (ctypes.c_uint32, [_VP]),
+    "tc_census_csr_noalloc": (ctypes.c_int, [_U32, _VP, _VP, _VP, _VP]),
     "tc_null_count": (tc_u128, [_U32, ctypes.POINTER(_U64)]),
     "tc_census_batch": (ctypes.c_int, [_VP, _U32, _VP, ctypes.POINTER(_U64), ctypes.POINTER(tc_u128)]),
     "tc_graph_stats": (ctypes.c_int, [_VP, ctypes.POINTER(tc_graph_info)]),
@@ -195,6 +196,16 @@ def tc_census_profile(g: int, d_out16, d_vcost, d_phase=None, stream=None, optio
         raise ValueError("d_out16 and d_vcost must be device memory")
     po, keepo = _options(options)
     _check(load().tc_census_profile(g, _stream_handle(stream), po, p, pv, pp or None), "tc_census_profile")
+
+
+def tc_census_csr_noalloc(n: int, d_off: int, d_adj: int, d_out16, stream=None) -> None:
+    """Census of a device CSR in the library's form using only the library's fixed scratch
+    array (no device allocation); d_off/d_adj are device pointers (ints), d_out16 a 16-element
+    uint64 device buffer."""
+    p, dev, keep = _buffer(d_out16, np.uint64)
+    if not dev:
+        raise ValueError("d_out16 must be device memory")
+    _check(load().tc_census_csr_noalloc(n, d_off, d_adj, _stream_handle(stream), p), "tc_census_csr_noalloc")
 
 
 def tc_census_grid(options=None) -> int:

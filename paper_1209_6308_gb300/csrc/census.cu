@@ -636,6 +636,29 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out) {
 
 int census_grid(const Opts& o) { return sm_count() * (int)o.ctas_per_sm; }
 
+tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
+                            uint32_t warp_end, uint32_t* ctr, unsigned long long* d_out16, cudaStream_t st) {
+    const size_t smem = census_smem(o.algo, o.chunk);
+    TC_TRY(prepare_device(st, (int)o.algo, smem));
+    Params P;
+    P.g = gd;
+    P.items = items;
+    P.n_items = n_items;
+    P.warp_begin = warp_begin;
+    P.warp_end = warp_end;
+    P.chunk = o.chunk;
+    P.warp_max = o.warp_max_deg;
+    P.ctr = ctr;
+    P.out = d_out16;
+    P.vcost = nullptr;
+    P.phase = nullptr;
+    const unsigned grid = (unsigned)census_grid(o);
+    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION><<<grid, kThreads, smem, st>>>(P);
+    else k_census<TC_ALGO_SUFFIX><<<grid, kThreads, smem, st>>>(P);
+    TC_LAUNCH("k_census");
+    return TC_OK;
+}
+
 tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16,
                          unsigned long long* d_vcost, unsigned long long* d_phase) {
     if (g.e_sym == 0) return TC_OK;

@@ -76,6 +76,10 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out);
 tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16,
                          unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr);
 int census_grid(const Opts& o);
+// Launch the census kernel on explicit buffers (no allocation): the work items, the id range
+// of the one-warp-per-vertex tier and 4 zeroed uint32 work counters are the caller's.
+tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
+                            uint32_t warp_end, uint32_t* ctr, unsigned long long* d_out16, cudaStream_t st);
 
 // The library's tricode -> class table (derived in tables.cu); census.cu copies it into
 // its device memory before the first census.
