@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-stride", type=int, default=0)
+    p.add_argument("--no-batch", action="store_true", help="skip the 4096-graph batched comparison")
+    p.add_argument("--autotune-trials", type=int, default=12)
     return p.parse_args()
 
 
@@ -186,6 +188,63 @@ def stored_traffic():
     return None
 
 
+def batched_comparison(tc, torch, sh, st, trials):
+    """4096 Chung-Lu graphs (n log-uniform in [32, 65536], exponent 2.1, mean degree 8, 10%
+    reciprocated, seed 4): per-graph launch loop vs one persistent graph-captured launch, default
+    and autotuned thresholds.  All three must give identical counts."""
+    import graphgen
+    specs = graphgen.batch_chung_lu(4096, 32, 65536, 8.0, 2.1, 0.1, 4)
+    arcs = int(sum(len(s) for (_, s, _) in specs))
+    opts = {"algo": tc.TC_ALGO_SUFFIX}
+    gs = [tc.Graph.from_arcs(n, s, d, stream=sh, options=opts) for (n, s, d) in specs]
+    handles = [g.handle for g in gs]
+    k = len(gs)
+    loop_out = torch.zeros(16 * k, dtype=torch.int64, device="cuda")
+    batch_out = torch.zeros(16 * k, dtype=torch.int64, device="cuda")
+
+    def timed(fn, reps):
+        fn()
+        st.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            st.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    def loop():
+        for i, h in enumerate(handles):
+            tc.tc_census_async(h, loop_out[16 * i:16 * i + 16], stream=sh)
+
+    loop_ms = timed(loop, 2)
+    b = tc.tc_batch_create(handles, stream=sh, options=opts)
+    try:
+        batch_ms = timed(lambda: tc.tc_batch_census_async(b, batch_out, stream=sh), 5)
+        same_default = bool(torch.equal(batch_out, loop_out))
+        t0 = time.perf_counter()
+        best, _ = tc.tc_batch_autotune(b, max_trials=trials, stream=sh)
+        tune_s = time.perf_counter() - t0
+        tuned_ms = timed(lambda: tc.tc_batch_census_async(b, batch_out, stream=sh), 5)
+        same_tuned = bool(torch.equal(batch_out, loop_out))
+        n_items, n_blocks = tc.tc_batch_stats(b)
+    finally:
+        tc.tc_batch_destroy(b)
+        for g in gs:
+            g.close()
+    return {"workload": "chunglu4096_n32-65536_g2.1_d8_r10_seed4", "graphs": k, "arcs": arcs,
+            "per_graph_loop": {"ms": loop_ms, "arcs_per_s": arcs / (loop_ms * 1e-3), "launches": k},
+            "persistent": {"ms": batch_ms, "arcs_per_s": arcs / (batch_ms * 1e-3), "launches": 1},
+            "persistent_autotuned": {"ms": tuned_ms, "arcs_per_s": arcs / (tuned_ms * 1e-3), "best": best,
+                                     "tuning_s": tune_s, "trials": trials},
+            "speedup_vs_loop": loop_ms / min(batch_ms, tuned_ms),
+            "items": n_items, "warp_blocks": n_blocks,
+            "counts_identical": same_default and same_tuned}
+
+
 def run_gpu(args):
     import torch
     import paper_1209_6308_gb300 as tc
@@ -288,6 +347,8 @@ def run_gpu(args):
         "step_ms": {"min": min(step_ms), "max": max(step_ms)},
         "timed_wall_s": wall,
     }
+    if not args.no_batch:
+        line["batched"] = batched_comparison(tc, torch, sh, stream, args.autotune_trials)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, s, d, arcs, args.cpu_sample_stride or CPU_STRIDE)
     print(json.dumps(line), flush=True)

@@ -50,6 +50,10 @@ def _load():
         lib.gg_loguniform_sizes.restype = None
         lib.gg_loguniform_sizes.argtypes = [ctypes.c_uint32, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32)]
+        lib.gg_chung_lu_batch.restype = ctypes.c_int64
+        lib.gg_chung_lu_batch.argtypes = [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_uint64, P32, P32,
+                                          ctypes.POINTER(ctypes.POINTER(ctypes.c_uint64))]
         lib.gg_free.argtypes = [ctypes.c_void_p]
         _lib = lib
     return _lib
@@ -96,9 +100,18 @@ def loguniform_sizes(k: int, lo: float, hi: float, seed: int) -> np.ndarray:
 
 def batch_chung_lu(k: int = 4096, lo: float = 32, hi: float = 65536, mean_deg: float = 8.0,
                    gamma: float = 2.1, recip: float = 0.1, seed: int = 4):
-    """k Chung-Lu graphs with log-uniform sizes: list of (n, src, dst)."""
+    """k Chung-Lu graphs with log-uniform sizes (graph i = chung_lu(n_i, ..., graph_index=i)),
+    generated in parallel: list of (n, src, dst)."""
     sizes = loguniform_sizes(k, lo, hi, seed)
-    return [chung_lu(int(n), mean_deg, gamma, recip, seed, i) for i, n in enumerate(sizes)]
+    lib = _load()
+    ps, pd = ctypes.POINTER(ctypes.c_uint32)(), ctypes.POINTER(ctypes.c_uint32)()
+    po = ctypes.POINTER(ctypes.c_uint64)()
+    tot = lib.gg_chung_lu_batch(k, sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), mean_deg, gamma, recip,
+                                seed, ctypes.byref(ps), ctypes.byref(pd), ctypes.byref(po))
+    src, dst = _take(lib, tot, ps, pd)
+    off = np.ctypeslib.as_array(po, shape=(k + 1,)).copy()
+    lib.gg_free(po)
+    return [(int(sizes[i]), src[off[i]:off[i + 1]], dst[off[i]:off[i + 1]]) for i in range(k)]
 
 
 def gnp(n: int, p: float, seed: int):

@@ -226,3 +226,40 @@ void gg_loguniform_sizes(uint32_t k, double lo, double hi, uint64_t seed, uint32
         out[i] = (uint32_t)v;
     }
 }
+
+/* k Chung-Lu graphs of sizes n[i] (graph i uses sub-stream i), generated in parallel.
+ * Arcs of graph i are written to src/dst [arc_off[i], arc_off[i+1]); returns the total arc
+ * count or -1.  The caller frees *src_out, *dst_out, *arc_off_out with gg_free. */
+int64_t gg_chung_lu_batch(uint32_t k, const uint32_t* n, double mean_deg, double gamma, double recip, uint64_t seed,
+                          uint32_t** src_out, uint32_t** dst_out, uint64_t** arc_off_out) {
+    uint32_t** ss = (uint32_t**)calloc(k ? k : 1, sizeof(uint32_t*));
+    uint32_t** dd = (uint32_t**)calloc(k ? k : 1, sizeof(uint32_t*));
+    int64_t* cnt = (int64_t*)calloc(k ? k : 1, sizeof(int64_t));
+    uint64_t* off = (uint64_t*)malloc(sizeof(uint64_t) * (k + 1ull));
+    if (!ss || !dd || !cnt || !off) { free(ss); free(dd); free(cnt); free(off); return -1; }
+    int failed = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : failed)
+    for (int64_t i = 0; i < (int64_t)k; ++i) {
+        cnt[i] = gg_chung_lu(n[i], mean_deg, gamma, recip, seed, (uint64_t)i, &ss[i], &dd[i]);
+        if (cnt[i] < 0) failed = 1;
+    }
+    int64_t tot = 0;
+    off[0] = 0;
+    for (uint32_t i = 0; i < k; ++i) { off[i + 1] = off[i] + (uint64_t)(cnt[i] > 0 ? cnt[i] : 0); }
+    tot = (int64_t)off[k];
+    uint32_t* so = (uint32_t*)malloc(sizeof(uint32_t) * (tot ? tot : 1));
+    uint32_t* d_o = (uint32_t*)malloc(sizeof(uint32_t) * (tot ? tot : 1));
+    if (!so || !d_o) failed = 1;
+    for (uint32_t i = 0; i < k; ++i) {
+        if (!failed && cnt[i] > 0) {
+            memcpy(so + off[i], ss[i], sizeof(uint32_t) * cnt[i]);
+            memcpy(d_o + off[i], dd[i], sizeof(uint32_t) * cnt[i]);
+        }
+        free(ss[i]);
+        free(dd[i]);
+    }
+    free(ss); free(dd); free(cnt);
+    if (failed) { free(so); free(d_o); free(off); return -1; }
+    *src_out = so; *dst_out = d_o; *arc_off_out = off;
+    return tot;
+}

@@ -134,11 +134,36 @@ uint32_t tc_census_grid(const tc_options* opt);
 /* Null count C(n,3) - sum(counts[1..15]) in 128-bit (Fig. 5 steps 3-5), on the host. */
 tc_u128 tc_null_count(uint32_t n, const uint64_t counts16[16]);
 
-/* Census of k graphs in one persistent launch.  out16xk receives 16 uint64 per graph
- * (index 0 set to the low 64 bits of the null count); out003_k (may be NULL) receives each
- * full 128-bit null count.  Host pointers.  Synchronises `stream`. */
+/* Census of k graphs in one persistent launch (builds a tc_batch, runs it once, frees it).
+ * out16xk receives 16 uint64 per graph in the callers' order (index 0 set to the low 64 bits
+ * of the null count); out003_k (may be NULL) receives each full 128-bit null count.  Host
+ * pointers.  Synchronises `stream`. */
 tc_status tc_census_batch(tc_graph* const* gs, uint32_t k, void* stream, uint64_t* out16xk,
                           tc_u128* out003_k);
+
+/* A reusable batch: one combined work plan for the k graphs (largest graph first; CTA items of
+ * every graph, then one-warp-per-vertex blocks of every graph, drawn by one persistent launch
+ * from two device work counters) and that launch captured in a CUDA graph.  The graphs must
+ * outlive the batch.  opt may be NULL (the defaults of tc_options).  Synchronises `stream`. */
+typedef struct tc_batch tc_batch;
+tc_status tc_batch_create(tc_graph* const* gs, uint32_t k, const tc_options* opt, void* stream, tc_batch** out);
+
+/* Replay the captured launch on `stream`; if d_out16xk (device, 16 uint64 per graph) is not
+ * NULL the counts of classes 1..15 (index 0 = 0) are copied there in the callers' order. */
+tc_status tc_batch_census_async(tc_batch* b, void* stream, uint64_t* d_out16xk);
+
+/* Replay and return host counts as for tc_census_batch.  Synchronises `stream`. */
+tc_status tc_batch_census(tc_batch* b, void* stream, uint64_t* out16xk, tc_u128* out003_k);
+
+/* Autotuner: time the batch under candidate tile and tier thresholds (warp_max_deg,
+ * chunk_entries, ctas_per_sm, item_work; at most max_trials of them, 0 = all), keep the
+ * fastest plan in the batch and report its options and median time per launch in ms. */
+tc_status tc_batch_autotune(tc_batch* b, void* stream, uint32_t max_trials, tc_options* best, float* best_ms);
+
+/* Work counts of the batch's current plan (either pointer may be NULL). */
+tc_status tc_batch_stats(const tc_batch* b, uint32_t* n_items, uint32_t* n_warp_blocks);
+
+void tc_batch_destroy(tc_batch* b);
 
 tc_status tc_graph_stats(const tc_graph* g, tc_graph_info* info);
 

@@ -69,6 +69,12 @@ SIGNATURES = {
     "tc_census_csr_noalloc": (ctypes.c_int, [_U32, _VP, _VP, _VP, _VP]),
     "tc_null_count": (tc_u128, [_U32, ctypes.POINTER(_U64)]),
     "tc_census_batch": (ctypes.c_int, [_VP, _U32, _VP, ctypes.POINTER(_U64), ctypes.POINTER(tc_u128)]),
+    "tc_batch_create": (ctypes.c_int, [_VP, _U32, _VP, _VP, ctypes.POINTER(_VP)]),
+    "tc_batch_census_async": (ctypes.c_int, [_VP, _VP, _VP]),
+    "tc_batch_census": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_U64), ctypes.POINTER(tc_u128)]),
+    "tc_batch_autotune": (ctypes.c_int, [_VP, _VP, _U32, _VP, ctypes.POINTER(ctypes.c_float)]),
+    "tc_batch_stats": (ctypes.c_int, [_VP, ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
+    "tc_batch_destroy": (None, [_VP]),
     "tc_graph_stats": (ctypes.c_int, [_VP, ctypes.POINTER(tc_graph_info)]),
     "tc_graph_device_csr": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "tc_graph_export_csr": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -231,6 +237,60 @@ def tc_census_batch(graphs, stream=None) -> list:
         row[0] = z[i].value()
         res.append(row)
     return res
+
+
+def tc_batch_create(graphs, stream=None, options=None) -> int:
+    """Reusable batched census over graph handles (one persistent, graph-captured launch)."""
+    k = len(graphs)
+    arr = (_VP * max(k, 1))(*graphs)
+    po, keep = _options(options)
+    out = _VP()
+    _check(load().tc_batch_create(ctypes.cast(arr, _VP), k, po, _stream_handle(stream), ctypes.byref(out)),
+           "tc_batch_create")
+    return out.value
+
+
+def tc_batch_census_async(b: int, d_out16xk=None, stream=None) -> None:
+    p = 0
+    if d_out16xk is not None:
+        p, dev, keep = _buffer(d_out16xk, np.uint64)
+        if not dev:
+            raise ValueError("d_out16xk must be device memory")
+    _check(load().tc_batch_census_async(b, _stream_handle(stream), p or None), "tc_batch_census_async")
+
+
+def tc_batch_census(b: int, k: int, stream=None) -> list:
+    out = (ctypes.c_uint64 * (16 * max(k, 1)))()
+    z = (tc_u128 * max(k, 1))()
+    _check(load().tc_batch_census(b, _stream_handle(stream), out, z), "tc_batch_census")
+    res = []
+    for i in range(k):
+        row = [int(out[16 * i + t]) for t in range(16)]
+        row[0] = z[i].value()
+        res.append(row)
+    return res
+
+
+def tc_batch_autotune(b: int, max_trials: int = 0, stream=None):
+    """Returns (best options dict, median ms per launch); the batch keeps the best plan."""
+    o = tc_options()
+    ms = ctypes.c_float()
+    _check(load().tc_batch_autotune(b, _stream_handle(stream), max_trials, ctypes.addressof(o), ctypes.byref(ms)),
+           "tc_batch_autotune")
+    best = {k: int(getattr(o, k)) for k in ("algo", "schedule", "warp_max_deg", "chunk_entries", "item_work",
+                                             "ctas_per_sm")}
+    return best, float(ms.value)
+
+
+def tc_batch_stats(b: int):
+    ni, nw = _U32(), _U32()
+    _check(load().tc_batch_stats(b, ctypes.byref(ni), ctypes.byref(nw)), "tc_batch_stats")
+    return int(ni.value), int(nw.value)
+
+
+def tc_batch_destroy(b: int) -> None:
+    if b:
+        load().tc_batch_destroy(b)
 
 
 def tc_graph_stats(g: int) -> dict:

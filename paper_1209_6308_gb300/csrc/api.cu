@@ -6,9 +6,6 @@
 
 #include "graph.cuh"
 
-struct tc_graph {
-    tc::GraphStore s;
-};
 
 namespace tc {
 
@@ -346,34 +343,5 @@ tc_status tc_census_opts(tc_graph* g, void* stream, const tc_options* opt, tc_u1
 }
 
 tc_status tc_census(tc_graph* g, void* stream, tc_u128 out[16]) { return tc_census_opts(g, stream, nullptr, out); }
-
-// Per-graph launches on one stream into one device array, one copy back (the batched
-// persistent form lives in batch.cu when built; this is the reference loop).
-tc_status tc_census_batch(tc_graph* const* gs, uint32_t k, void* stream, uint64_t* out16xk, tc_u128* out003_k) {
-    if (!gs || !out16xk) return fail(TC_ERR_ARG, "null argument");
-    if (k == 0) return TC_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    DevBuf d;
-    TC_TRY(d.alloc(sizeof(unsigned long long) * 16ull * k, st));
-    TC_CUDA(cudaMemsetAsync(d.p, 0, sizeof(unsigned long long) * 16ull * k, st));
-    for (uint32_t i = 0; i < k; ++i) {
-        if (!gs[i]) return fail(TC_ERR_ARG, "null graph in batch");
-        Opts o;
-        TC_TRY(resolve_opts(nullptr, &gs[i]->s.opts, &o));
-        Plan* p = nullptr;
-        TC_TRY(get_plan(gs[i]->s, o, st, &p));
-        TC_TRY(census_enqueue(gs[i]->s, o, *p, st, d.as<unsigned long long>() + 16ull * i));
-    }
-    TC_CUDA(cudaMemcpyAsync(out16xk, d.p, sizeof(unsigned long long) * 16ull * k, cudaMemcpyDeviceToHost, st));
-    TC_CUDA(cudaStreamSynchronize(st));
-    for (uint32_t i = 0; i < k; ++i) {
-        uint64_t* c = out16xk + 16ull * i;
-        c[0] = 0;
-        tc_u128 z = tc_null_count(gs[i]->s.n, c);
-        c[0] = z.lo;
-        if (out003_k) out003_k[i] = z;
-    }
-    return TC_OK;
-}
 
 }  // extern "C"

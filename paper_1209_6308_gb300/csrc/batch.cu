@@ -1,0 +1,388 @@
+// batch.cu - census of many graphs in one persistent launch (the batched form of the Fig. 5
+// census), with its combined work plan built on the device, the launch captured once in a
+// CUDA graph and replayed, and an autotuner for the tile and tier thresholds.
+//
+// Plan: the graphs are ordered by size (largest first, so the longest items start first);
+// each graph's vertices with degree above the warp-tier threshold become CTA items exactly as
+// in the single-graph plan, tagged with the graph index, and its remaining active vertices
+// become (u0, u1, graph) blocks of 32 for the one-warp-per-vertex tier.  One launch runs
+// every item of every graph, then every block, from two device-side work counters.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "graph.cuh"
+
+namespace tc {
+namespace {
+
+__device__ __forceinline__ uint32_t graph_of(const uint64_t* __restrict__ pre, uint32_t k, uint64_t i) {
+    uint32_t lo = 0, hi = k;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// wide[g] = vertices of graph g with degree > warp_max (a prefix of its ids)
+__global__ void k_batch_wide(const GraphDev* __restrict__ gs, const uint64_t* __restrict__ voff, uint32_t k,
+                             uint64_t total, uint32_t warp_max, uint32_t* wide) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = graph_of(voff, k, i);
+        const uint64_t x = i - voff[g];
+        const uint64_t* off = gs[g].off;
+        if (off[x + 1] - off[x] > warp_max) atomicAdd(&wide[g], 1u);
+    }
+}
+
+// Items per wide vertex (same sizing as the single-graph plain plan, per-graph mean degree).
+__global__ void k_batch_count(const GraphDev* __restrict__ gs, const uint64_t* __restrict__ woff, uint32_t k,
+                              uint64_t total, uint32_t chunk, uint32_t item_work, int algo,
+                              const float* __restrict__ dbar, uint32_t* cnt) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = graph_of(woff, k, i);
+        const uint64_t x = i - woff[g];
+        const GraphDev G = gs[g];
+        const uint32_t du = (uint32_t)(G.off[x + 1] - G.off[x]);
+        const uint32_t P = du - G.up[x];
+        if (P == 0) { cnt[i] = 0; continue; }
+        const uint32_t C = (du + chunk - 1) / chunk;
+        double est = (double)P * ((double)dbar[g] + 16.0 + 16.0 * (double)C) +
+                     (algo == TC_ALGO_UNION ? 0.5 * (double)P * (double)du : 0.0);
+        double s = ceil(est / (double)item_work);
+        const double smin = ceil((double)P / (double)kMaxItemPairs);
+        if (s < smin) s = smin;
+        if (s < 1.0) s = 1.0;
+        if (s > (double)P) s = (double)P;
+        cnt[i] = (uint32_t)s;
+    }
+}
+
+__global__ void k_batch_emit(const GraphDev* __restrict__ gs, const uint64_t* __restrict__ woff, uint32_t k,
+                             uint64_t total, const uint32_t* __restrict__ pos, const uint32_t* __restrict__ cnt,
+                             Item* items) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t S = cnt[i];
+        if (!S) continue;
+        const uint32_t g = graph_of(woff, k, i);
+        const uint32_t x = (uint32_t)(i - woff[g]);
+        const GraphDev G = gs[g];
+        const uint32_t du = (uint32_t)(G.off[x + 1] - G.off[x]);
+        const uint32_t up = G.up[x], P = du - up;
+        uint32_t o = pos[i];
+        for (uint32_t s = 0; s < S; ++s) {
+            Item it;
+            it.u = x;
+            it.j0 = up + (uint32_t)((uint64_t)P * s / S);
+            it.j1 = up + (uint32_t)((uint64_t)P * (s + 1) / S);
+            it.pad = g;
+            items[o++] = it;
+        }
+    }
+}
+
+// launch-order outputs -> callers' order
+__global__ void k_batch_scatter(const unsigned long long* __restrict__ src, const uint32_t* __restrict__ order,
+                                uint32_t k, unsigned long long* dst) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < 16ull * k; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[16ull * order[i / 16] + (i % 16)] = src[i];
+}
+
+}  // namespace
+
+struct BatchStore {
+    uint32_t k = 0;
+    std::vector<tc_graph*> graphs;      // in launch order (largest first)
+    std::vector<uint32_t> order;        // launch position -> caller's index
+    Opts opts;
+    cudaStream_t cap = nullptr;         // stream used only to capture the launch
+    DevBuf d_graphs, d_voff, d_woff, d_dbar, d_wide, d_order, items, wblocks, ctr, out;
+    uint32_t n_items = 0, n_wblocks = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long* h_out = nullptr;
+    std::vector<uint64_t> woff_h;
+
+    ~BatchStore() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (h_out) cudaFreeHost(h_out);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+namespace {
+
+// (Re)build the combined plan for b.opts and capture its launch.
+tc_status batch_plan(BatchStore& b, cudaStream_t st) {
+    const Opts& o = b.opts;
+    const uint32_t k = b.k;
+    if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+    if (b.graph) { cudaGraphDestroy(b.graph); b.graph = nullptr; }
+    // per-graph vertex prefix and wide counts
+    std::vector<uint64_t> voff(k + 1, 0);
+    std::vector<float> dbar(k);
+    for (uint32_t i = 0; i < k; ++i) {
+        const GraphStore& g = b.graphs[i]->s;
+        voff[i + 1] = voff[i] + g.n;
+        dbar[i] = g.n_active ? (float)(2.0 * (double)g.e_sym / (double)g.n_active) : 0.f;
+    }
+    TC_TRY(b.d_voff.alloc_persistent(sizeof(uint64_t) * (k + 1)));
+    TC_CUDA(cudaMemcpyAsync(b.d_voff.p, voff.data(), sizeof(uint64_t) * (k + 1), cudaMemcpyHostToDevice, st));
+    TC_TRY(b.d_dbar.alloc_persistent(sizeof(float) * k));
+    TC_CUDA(cudaMemcpyAsync(b.d_dbar.p, dbar.data(), sizeof(float) * k, cudaMemcpyHostToDevice, st));
+    TC_TRY(b.d_wide.alloc_persistent(sizeof(uint32_t) * k));
+    TC_CUDA(cudaMemsetAsync(b.d_wide.p, 0, sizeof(uint32_t) * k, st));
+    if (voff[k]) {
+        k_batch_wide<<<grid_for(voff[k], 256, 1u << 16), 256, 0, st>>>(b.d_graphs.as<GraphDev>(), b.d_voff.as<uint64_t>(),
+                                                                      k, voff[k], o.warp_max_deg, b.d_wide.as<uint32_t>());
+        TC_LAUNCH("k_batch_wide");
+    }
+    std::vector<uint32_t> wide(k);
+    TC_CUDA(cudaMemcpyAsync(wide.data(), b.d_wide.p, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    // CTA items of the wide vertices of every graph
+    b.woff_h.assign(k + 1, 0);
+    for (uint32_t i = 0; i < k; ++i) b.woff_h[i + 1] = b.woff_h[i] + wide[i];
+    const uint64_t total_w = b.woff_h[k];
+    TC_TRY(b.d_woff.alloc_persistent(sizeof(uint64_t) * (k + 1)));
+    TC_CUDA(cudaMemcpyAsync(b.d_woff.p, b.woff_h.data(), sizeof(uint64_t) * (k + 1), cudaMemcpyHostToDevice, st));
+    b.n_items = 0;
+    if (total_w) {
+        if (total_w >= (1ull << 32)) return fail(TC_ERR_RANGE, "batch has too many wide vertices");
+        DevBuf cnt, pos, tot;
+        TC_TRY(cnt.alloc(sizeof(uint32_t) * total_w, st));
+        TC_TRY(pos.alloc(sizeof(uint32_t) * total_w, st));
+        TC_TRY(tot.alloc(sizeof(uint32_t), st));
+        k_batch_count<<<grid_for(total_w, 256, 1u << 16), 256, 0, st>>>(b.d_graphs.as<GraphDev>(), b.d_woff.as<uint64_t>(), k,
+                                                                       total_w, o.chunk, o.item_work, (int)o.algo,
+                                                                       b.d_dbar.as<float>(), cnt.as<uint32_t>());
+        TC_LAUNCH("k_batch_count");
+        TC_TRY(scan_u32(cnt.as<uint32_t>(), pos.as<uint32_t>(), total_w, tot.as<uint32_t>(), st));
+        TC_CUDA(cudaMemcpyAsync(&b.n_items, tot.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        TC_TRY(b.items.alloc_persistent(sizeof(Item) * (b.n_items ? b.n_items : 1)));
+        if (b.n_items) {
+            k_batch_emit<<<grid_for(total_w, 256, 1u << 16), 256, 0, st>>>(b.d_graphs.as<GraphDev>(), b.d_woff.as<uint64_t>(),
+                                                                          k, total_w, pos.as<uint32_t>(),
+                                                                          cnt.as<uint32_t>(), b.items.as<Item>());
+            TC_LAUNCH("k_batch_emit");
+        }
+        TC_CUDA(cudaStreamSynchronize(st));
+    } else {
+        TC_TRY(b.items.alloc_persistent(sizeof(Item)));
+    }
+    // warp-tier blocks (32 vertices each) of every graph
+    std::vector<uint4> wb;
+    for (uint32_t i = 0; i < k; ++i) {
+        const uint32_t act = b.graphs[i]->s.n_active;
+        for (uint32_t u = wide[i]; u < act; u += 32) wb.push_back(make_uint4(u, std::min(u + 32u, act), i, 0u));
+    }
+    b.n_wblocks = (uint32_t)wb.size();
+    TC_TRY(b.wblocks.alloc_persistent(sizeof(uint4) * (wb.empty() ? 1 : wb.size())));
+    if (!wb.empty())
+        TC_CUDA(cudaMemcpyAsync(b.wblocks.p, wb.data(), sizeof(uint4) * wb.size(), cudaMemcpyHostToDevice, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    // capture: zero counters and outputs, launch
+    TC_TRY(census_prepare(st, o));
+    TC_CUDA(cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeThreadLocal));
+    tc_status s = TC_OK;
+    if (cudaMemsetAsync(b.ctr.p, 0, sizeof(uint32_t) * 4, b.cap) != cudaSuccess ||
+        cudaMemsetAsync(b.out.p, 0, sizeof(unsigned long long) * 16ull * k, b.cap) != cudaSuccess)
+        s = fail(TC_ERR_CUDA, "batch capture: memset failed");
+    if (s == TC_OK)
+        s = census_launch_batch(b.d_graphs.as<GraphDev>(), b.items.as<Item>(), b.n_items, b.wblocks.as<uint4>(),
+                                b.n_wblocks, o, b.ctr.as<uint32_t>(), b.out.as<unsigned long long>(), b.cap);
+    cudaGraph_t gph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b.cap, &gph);
+    if (s != TC_OK) {
+        if (gph) cudaGraphDestroy(gph);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    b.graph = gph;
+    TC_CUDA(cudaGraphInstantiate(&b.exec, b.graph, 0));
+    return TC_OK;
+}
+
+tc_status batch_run(BatchStore& b, cudaStream_t st) {
+    if (b.k == 0) return TC_OK;
+    TC_CUDA(cudaGraphLaunch(b.exec, st));
+    return TC_OK;
+}
+
+}  // namespace
+}  // namespace tc
+
+struct tc_batch {
+    tc::BatchStore s;
+};
+
+using namespace tc;
+
+extern "C" {
+
+tc_status tc_batch_create(tc_graph* const* gs, uint32_t k, const tc_options* opt, void* stream, tc_batch** out) {
+    if (!out || (k && !gs)) return fail(TC_ERR_ARG, "null argument");
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    tc_batch* b = new tc_batch();
+    BatchStore& B = b->s;
+    B.k = k;
+    tc_status s = resolve_opts(opt, nullptr, &B.opts);
+    for (uint32_t i = 0; s == TC_OK && i < k; ++i)
+        if (!gs[i]) s = fail(TC_ERR_ARG, "null graph in batch");
+    if (s == TC_OK) {
+        B.order.resize(k);
+        std::iota(B.order.begin(), B.order.end(), 0u);
+        std::stable_sort(B.order.begin(), B.order.end(),
+                         [&](uint32_t a, uint32_t c) { return gs[a]->s.e_sym > gs[c]->s.e_sym; });
+        for (uint32_t i = 0; i < k; ++i) B.graphs.push_back(gs[B.order[i]]);
+        std::vector<GraphDev> gd(k);
+        for (uint32_t i = 0; i < k; ++i) gd[i] = B.graphs[i]->s.dev();
+        s = B.d_graphs.alloc_persistent(sizeof(GraphDev) * (k ? k : 1));
+        if (s == TC_OK && k && cudaMemcpy(B.d_graphs.p, gd.data(), sizeof(GraphDev) * k, cudaMemcpyHostToDevice) != cudaSuccess)
+            s = fail(TC_ERR_CUDA, "batch: upload of graph table failed");
+        if (s == TC_OK) s = B.d_order.alloc_persistent(sizeof(uint32_t) * (k ? k : 1));
+        if (s == TC_OK && k &&
+            cudaMemcpy(B.d_order.p, B.order.data(), sizeof(uint32_t) * k, cudaMemcpyHostToDevice) != cudaSuccess)
+            s = fail(TC_ERR_CUDA, "batch: upload of graph order failed");
+        if (s == TC_OK) s = B.ctr.alloc_persistent(sizeof(uint32_t) * 4);
+        if (s == TC_OK) s = B.out.alloc_persistent(sizeof(unsigned long long) * 16ull * (k ? k : 1));
+        if (s == TC_OK && cudaMallocHost(&B.h_out, sizeof(unsigned long long) * 16ull * (k ? k : 1)) != cudaSuccess)
+            s = fail(TC_ERR_OOM, "batch: pinned host buffer");
+        if (s == TC_OK && cudaStreamCreateWithFlags(&B.cap, cudaStreamNonBlocking) != cudaSuccess)
+            s = fail(TC_ERR_CUDA, "batch: capture stream");
+        if (s == TC_OK && k) s = batch_plan(B, st);
+    }
+    if (s != TC_OK) {
+        std::string keep = tc_last_error();
+        delete b;
+        set_error(keep);
+        return s;
+    }
+    *out = b;
+    return TC_OK;
+}
+
+tc_status tc_batch_census_async(tc_batch* b, void* stream, uint64_t* d_out16xk) {
+    if (!b) return fail(TC_ERR_ARG, "null batch");
+    cudaStream_t st = (cudaStream_t)stream;
+    TC_TRY(batch_run(b->s, st));
+    if (d_out16xk && b->s.k) {
+        // the launch writes in size order; scatter back to the caller's order
+        k_batch_scatter<<<grid_for(16ull * b->s.k, 256, 4096), 256, 0, st>>>(
+            b->s.out.as<unsigned long long>(), b->s.d_order.as<uint32_t>(), b->s.k,
+            reinterpret_cast<unsigned long long*>(d_out16xk));
+        TC_LAUNCH("k_batch_scatter");
+    }
+    return TC_OK;
+}
+
+tc_status tc_batch_census(tc_batch* b, void* stream, uint64_t* out16xk, tc_u128* out003_k) {
+    if (!b || !out16xk) return fail(TC_ERR_ARG, "null argument");
+    BatchStore& B = b->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (B.k == 0) return TC_OK;
+    TC_TRY(batch_run(B, st));
+    TC_CUDA(cudaMemcpyAsync(B.h_out, B.out.p, sizeof(unsigned long long) * 16ull * B.k, cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    for (uint32_t i = 0; i < B.k; ++i) {
+        uint64_t* c = out16xk + 16ull * B.order[i];
+        for (int t = 0; t < 16; ++t) c[t] = B.h_out[16ull * i + t];
+        c[0] = 0;
+        tc_u128 z = tc_null_count(B.graphs[i]->s.n, c);
+        c[0] = z.lo;
+        if (out003_k) out003_k[B.order[i]] = z;
+    }
+    return TC_OK;
+}
+
+tc_status tc_batch_autotune(tc_batch* b, void* stream, uint32_t max_trials, tc_options* best_out, float* best_ms) {
+    if (!b) return fail(TC_ERR_ARG, "null batch");
+    BatchStore& B = b->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (B.k == 0) return TC_OK;
+    const Opts base = B.opts;
+    // the current plan first, then the grid of tile and tier thresholds
+    std::vector<Opts> cand{base};
+    for (uint32_t wm : {16u, 32u, 64u})
+        for (uint32_t ch : {2048u, 4096u})
+            for (uint32_t cps : {3u, 4u})
+                for (uint32_t iw : {1u << 16, 1u << 18}) {
+                    Opts o = base;
+                    o.warp_max_deg = wm;
+                    o.chunk = ch;
+                    o.ctas_per_sm = cps;
+                    o.item_work = iw;
+                    if (!(o == base)) cand.push_back(o);
+                }
+    if (max_trials && max_trials < cand.size()) cand.resize(max_trials);
+    cudaEvent_t e0, e1;
+    TC_CUDA(cudaEventCreate(&e0));
+    TC_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Opts best_o = base;
+    tc_status s = TC_OK;
+    for (const Opts& o : cand) {
+        B.opts = o;
+        s = batch_plan(B, st);
+        if (s != TC_OK) break;
+        float ts[3];
+        for (int r = 0; r < 4 && s == TC_OK; ++r) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) s = fail(TC_ERR_CUDA, "event");
+            if (s == TC_OK) s = batch_run(B, st);
+            if (s == TC_OK && cudaEventRecord(e1, st) != cudaSuccess) s = fail(TC_ERR_CUDA, "event");
+            if (s == TC_OK && cudaEventSynchronize(e1) != cudaSuccess) s = fail(TC_ERR_CUDA, "event sync");
+            if (s == TC_OK && r > 0) cudaEventElapsedTime(&ts[r - 1], e0, e1);
+        }
+        if (s != TC_OK) break;
+        std::sort(ts, ts + 3);
+        if (ts[1] < best) { best = ts[1]; best_o = o; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B.opts = best_o;
+    TC_TRY(batch_plan(B, st));
+    if (s != TC_OK) return s;
+    if (best_out) {
+        std::memset(best_out, 0, sizeof(*best_out));
+        best_out->algo = best_o.algo;
+        best_out->schedule = best_o.schedule;
+        best_out->warp_max_deg = best_o.warp_max_deg;
+        best_out->chunk_entries = best_o.chunk;
+        best_out->item_work = best_o.item_work;
+        best_out->ctas_per_sm = best_o.ctas_per_sm;
+    }
+    if (best_ms) *best_ms = best;
+    return TC_OK;
+}
+
+tc_status tc_batch_stats(const tc_batch* b, uint32_t* n_items, uint32_t* n_warp_blocks) {
+    if (!b) return fail(TC_ERR_ARG, "null batch");
+    if (n_items) *n_items = b->s.n_items;
+    if (n_warp_blocks) *n_warp_blocks = b->s.n_wblocks;
+    return TC_OK;
+}
+
+void tc_batch_destroy(tc_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    delete b;
+}
+
+// One-shot batched census: build the batch, run it once, destroy it.
+tc_status tc_census_batch(tc_graph* const* gs, uint32_t k, void* stream, uint64_t* out16xk, tc_u128* out003_k) {
+    if (!gs || !out16xk) return fail(TC_ERR_ARG, "null argument");
+    if (k == 0) return TC_OK;
+    tc_batch* b = nullptr;
+    TC_TRY(tc_batch_create(gs, k, nullptr, stream, &b));
+    tc_status s = tc_batch_census(b, stream, out16xk, out003_k);
+    tc_batch_destroy(b);
+    return s;
+}
+
+}  // extern "C"

@@ -28,6 +28,7 @@
 // N[v] entry is read once per pair with no search.  Vertices with smaller degree are
 // handled one warp per vertex after the items run out, in the same persistent launch.
 #include <atomic>
+#include <cstring>
 
 #include "graph.cuh"
 
@@ -59,6 +60,11 @@ struct Params {
     unsigned long long* out;       // 16 accumulators
     unsigned long long* vcost;     // optional [n]: SM cycles spent per vertex u (items summed)
     unsigned long long* phase;     // optional [3 * gridDim]: globaltimer at start, end of items, end
+    // batched launch: item.pad is the graph index, warp-tier blocks are (u0, u1, graph), and
+    // graph g's counts go to out[16 g ..]
+    const GraphDev* graphs;
+    const uint4* wblocks;
+    uint32_t n_wblocks;
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -221,7 +227,14 @@ __device__ __forceinline__ uint32_t v_side_chunk(const uint32_t* __restrict__ B,
     return k0;
 }
 
-template <int ALGO>
+// Lanes 0-15 add their class totals to graph output `out` (batched launches switch graphs).
+__device__ __forceinline__ void flush_graph(Counts& k, int lane, unsigned long long* out) {
+    pk_flush(k, lane);
+    if (lane < 16 && k.racc) atomicAdd(&out[lane], k.racc);
+    k.racc = 0;
+}
+
+template <int ALGO, bool BATCH = false>
 __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t chunk = P.chunk;
@@ -244,15 +257,28 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     if (P.phase && tid == 0) P.phase[3 * blockIdx.x] = global_ns();
     __syncthreads();
 
-    const uint64_t n = P.g.n;
+    uint64_t n = P.g.n;
     const uint64_t* __restrict__ off = P.g.off;
     const uint32_t* __restrict__ adj = P.g.adj;
+    const uint32_t* __restrict__ upv = P.g.up;
+    uint32_t cur_graph = 0xffffffffu;          // batched: the graph whose totals the lanes hold
+    unsigned long long* gout = P.out;
     Counts cnt;
     cnt.lo = cnt.hi = cnt.racc = 0;
     cnt.trips = 0;
     PairAcc pa;
     pa.vo = pa.fo = 0;
     pa.cm = pa.trips = 0;
+    auto use_graph = [&](uint32_t gi) {
+        if (cur_graph != 0xffffffffu) flush_graph(cnt, lane, gout);
+        cur_graph = gi;
+        const GraphDev G = P.graphs[gi];
+        n = G.n;
+        off = G.off;
+        adj = G.adj;
+        upv = G.up;
+        gout = P.out + 16ull * gi;
+    };
 
     // ---------------------------------------------------------------- CTA items
     for (;;) {
@@ -261,6 +287,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
         const uint32_t it = s_item;
         if (it >= P.n_items) break;
         const Item w = P.items[it];
+        if (BATCH && w.pad != cur_graph) use_graph(w.pad);
         const long long t_item = clock64();
         const uint32_t u = w.u;
         const uint64_t ubase = off[u];
@@ -412,23 +439,35 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
             }
             __syncthreads();   // all warps are done with this chunk before it is replaced
         }
-        if (P.vcost && tid == 0) atomicAdd(&P.vcost[u], (unsigned long long)(clock64() - t_item));
+        if (!BATCH && P.vcost && tid == 0) atomicAdd(&P.vcost[u], (unsigned long long)(clock64() - t_item));
     }
     if (P.phase && tid == 0) P.phase[3 * blockIdx.x + 1] = global_ns();
 
     // ---------------------------------------------------------------- one warp per vertex
     uint32_t* wA = reinterpret_cast<uint32_t*>(smem) + warp * P.warp_max;
     for (;;) {
-        uint32_t ub = 0;
-        if (lane == 0) ub = atomicAdd(&P.ctr[1], 32u);
-        ub = __shfl_sync(0xffffffffu, ub, 0);
-        if (ub >= P.warp_end - P.warp_begin) break;
-        const uint32_t u0 = P.warp_begin + ub;
-        const uint32_t u1 = min(u0 + 32u, P.warp_end);
+        uint32_t u0, u1;
+        if (BATCH) {
+            uint32_t b = 0;
+            if (lane == 0) b = atomicAdd(&P.ctr[1], 1u);
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (b >= P.n_wblocks) break;
+            const uint4 wb = P.wblocks[b];
+            if (wb.z != cur_graph) use_graph(wb.z);
+            u0 = wb.x;
+            u1 = wb.y;
+        } else {
+            uint32_t ub = 0;
+            if (lane == 0) ub = atomicAdd(&P.ctr[1], 32u);
+            ub = __shfl_sync(0xffffffffu, ub, 0);
+            if (ub >= P.warp_end - P.warp_begin) break;
+            u0 = P.warp_begin + ub;
+            u1 = min(u0 + 32u, P.warp_end);
+        }
         for (uint32_t u = u0; u < u1; ++u) {
             const uint64_t ubase = off[u];
             const uint32_t du = (uint32_t)(off[u + 1] - ubase);
-            const uint32_t p0 = P.g.up[u];
+            const uint32_t p0 = upv[u];
             if (p0 >= du) continue;
             const long long t_vert = clock64();
             __syncwarp();
@@ -490,15 +529,19 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                     pair_fold(cnt, pa, lane, duv, cuv, sT, suf, n - du - dv);
                 }
             }
-            if (P.vcost && lane == 0) P.vcost[u] += (unsigned long long)(clock64() - t_vert);
+            if (!BATCH && P.vcost && lane == 0) P.vcost[u] += (unsigned long long)(clock64() - t_vert);
         }
     }
 
     // ---------------------------------------------------------------- totals
-    pk_flush(cnt, lane);
-    if (lane < 16 && cnt.racc) atomicAdd(&sC[lane], cnt.racc);
-    __syncthreads();
-    if (tid < 16 && sC[tid]) atomicAdd(&P.out[tid], sC[tid]);
+    if (BATCH) {
+        if (cur_graph != 0xffffffffu) flush_graph(cnt, lane, gout);
+    } else {
+        pk_flush(cnt, lane);
+        if (lane < 16 && cnt.racc) atomicAdd(&sC[lane], cnt.racc);
+        __syncthreads();
+        if (tid < 16 && sC[tid]) atomicAdd(&P.out[tid], sC[tid]);
+    }
     if (P.phase && tid == 0) P.phase[3 * blockIdx.x + 2] = global_ns();
 }
 
@@ -553,7 +596,7 @@ __global__ void k_plan_emit(GraphDev g, uint32_t u_end, const uint32_t* pos, con
 }
 
 std::atomic<uint64_t> g_table_uploaded{0};
-std::atomic<uint64_t> g_attr_set[2] = {{0}, {0}};
+std::atomic<uint64_t> g_attr_set[4] = {{0}, {0}, {0}, {0}};
 
 size_t census_smem(uint32_t algo, uint32_t chunk) {
     return sizeof(uint32_t) * (algo == TC_ALGO_UNION ? 3ull : 4ull) * chunk + sizeof(uint32_t) * (chunk / 16) +
@@ -576,10 +619,14 @@ tc_status prepare_device(cudaStream_t st, int algo, size_t smem) {
     TC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int limit = optin - 256;   // leave room for the kernel's static shared variables
     if ((int)smem > limit) return fail(TC_ERR_ARG, "chunk_entries too large for this GPU's shared memory");
-    if (!(g_attr_set[algo].load() & bit)) {
-        const void* fn = algo == TC_ALGO_UNION ? (const void*)k_census<TC_ALGO_UNION> : (const void*)k_census<TC_ALGO_SUFFIX>;
-        TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-        g_attr_set[algo].fetch_or(bit);
+    const void* fns[4] = {(const void*)k_census<TC_ALGO_UNION, false>, (const void*)k_census<TC_ALGO_SUFFIX, false>,
+                          (const void*)k_census<TC_ALGO_UNION, true>, (const void*)k_census<TC_ALGO_SUFFIX, true>};
+    for (int b = 0; b < 2; ++b) {
+        const int idx = 2 * b + algo;
+        if (!(g_attr_set[idx].load() & bit)) {
+            TC_CUDA(cudaFuncSetAttribute(fns[idx], cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+            g_attr_set[idx].fetch_or(bit);
+        }
     }
     return TC_OK;
 }
@@ -636,6 +683,29 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out) {
 
 int census_grid(const Opts& o) { return sm_count() * (int)o.ctas_per_sm; }
 
+tc_status census_launch_batch(const GraphDev* d_graphs, const Item* items, uint32_t n_items, const uint4* wblocks,
+                              uint32_t n_wblocks, const Opts& o, uint32_t* ctr, unsigned long long* d_out, cudaStream_t st) {
+    const size_t smem = census_smem(o.algo, o.chunk);
+    Params P;
+    std::memset(&P, 0, sizeof(P));
+    P.items = items;
+    P.n_items = n_items;
+    P.chunk = o.chunk;
+    P.warp_max = o.warp_max_deg;
+    P.ctr = ctr;
+    P.out = d_out;
+    P.graphs = d_graphs;
+    P.wblocks = wblocks;
+    P.n_wblocks = n_wblocks;
+    const unsigned grid = (unsigned)census_grid(o);
+    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, true><<<grid, kThreads, smem, st>>>(P);
+    else k_census<TC_ALGO_SUFFIX, true><<<grid, kThreads, smem, st>>>(P);
+    TC_LAUNCH("k_census (batched)");
+    return TC_OK;
+}
+
+tc_status census_prepare(cudaStream_t st, const Opts& o) { return prepare_device(st, (int)o.algo, census_smem(o.algo, o.chunk)); }
+
 tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
                             uint32_t warp_end, uint32_t* ctr, unsigned long long* d_out16, cudaStream_t st) {
     const size_t smem = census_smem(o.algo, o.chunk);
@@ -652,6 +722,9 @@ tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items
     P.out = d_out16;
     P.vcost = nullptr;
     P.phase = nullptr;
+    P.graphs = nullptr;
+    P.wblocks = nullptr;
+    P.n_wblocks = 0;
     const unsigned grid = (unsigned)census_grid(o);
     if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION><<<grid, kThreads, smem, st>>>(P);
     else k_census<TC_ALGO_SUFFIX><<<grid, kThreads, smem, st>>>(P);
@@ -677,6 +750,9 @@ tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream
     P.out = d_out16;
     P.vcost = d_vcost;
     P.phase = d_phase;
+    P.graphs = nullptr;
+    P.wblocks = nullptr;
+    P.n_wblocks = 0;
     const unsigned grid = (unsigned)census_grid(o);
     if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION><<<grid, kThreads, smem, st>>>(P);
     else k_census<TC_ALGO_SUFFIX><<<grid, kThreads, smem, st>>>(P);

@@ -64,6 +64,14 @@ struct GraphStore {
     }
 };
 
+}  // namespace tc
+
+struct tc_graph {
+    tc::GraphStore s;
+};
+
+namespace tc {
+
 tc_status build_from_arcs(GraphStore& g, uint64_t m, const uint32_t* d_src, const uint32_t* d_dst, cudaStream_t st);
 tc_status build_from_csr(GraphStore& g, const uint64_t* d_off, const uint32_t* d_adj, cudaStream_t st);
 
@@ -76,6 +84,13 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out);
 tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16,
                          unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr);
 int census_grid(const Opts& o);
+// Batched census: one launch over several graphs (d_graphs on the device); item.pad is the
+// graph index, wblocks are (u0, u1, graph, 0) warp-tier blocks; graph g's counts are added to
+// d_out[16 g ..] (caller-zeroed); ctr: 4 zeroed uint32.  census_prepare must have run.
+tc_status census_launch_batch(const GraphDev* d_graphs, const Item* items, uint32_t n_items, const uint4* wblocks,
+                              uint32_t n_wblocks, const Opts& o, uint32_t* ctr, unsigned long long* d_out, cudaStream_t st);
+// Per-device set-up of the census kernels (table upload, shared-memory limit); synchronises st.
+tc_status census_prepare(cudaStream_t st, const Opts& o);
 // Launch the census kernel on explicit buffers (no allocation): the work items, the id range
 // of the one-warp-per-vertex tier and 4 zeroed uint32 work counters are the caller's.
 tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
