@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--cpu-sample-stride", type=int, default=0)
     p.add_argument("--no-batch", action="store_true", help="skip the 4096-graph batched comparison")
     p.add_argument("--autotune-trials", type=int, default=12)
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-schedule comparison")
     return p.parse_args()
 
 
@@ -245,6 +246,25 @@ def batched_comparison(tc, torch, sh, st, trials):
             "counts_identical": same_default and same_tuned}
 
 
+def learned_comparison(tc, g, stream):
+    """Cost model trained on R-MAT scales 18-22 (seeds 18-22) from cycles the plain census
+    measures, attached to the bench graph: census time with the plain and the learned schedule
+    (identical counts required) and the held-out cost-prediction error of both."""
+    from paper_1209_6308_gb300 import learned
+    model, info = learned.train_cost_model(scales=(18, 19, 20, 21, 22), steps=800, stream=stream.cuda_stream)
+    try:
+        learned.attach(model, g, stream=stream.cuda_stream)
+        plain_ms, plain_c = learned.census_ms(g, learned.PLAIN, stream)
+        learned_ms, learned_c = learned.census_ms(g, learned.LEARNED, stream)
+        q = learned.prediction_quality(model, g, stream=stream.cuda_stream)
+    finally:
+        tc.tc_costmodel_destroy(model)
+    return {"training": info, "plain_ms": plain_ms, "learned_ms": learned_ms,
+            "speedup": plain_ms / learned_ms, "counts_identical": plain_c == learned_c,
+            "heldout_rms_log_cycle_error": {"model": q["rms_log_err_model"], "degree": q["rms_log_err_degree"],
+                                            "vertices": q["vertices"]}}
+
+
 def run_gpu(args):
     import torch
     import paper_1209_6308_gb300 as tc
@@ -303,6 +323,9 @@ def run_gpu(args):
     # end to end through the C ABI from pinned host buffers
     src_pin = torch.from_numpy(s.view("int32")).pin_memory()
     dst_pin = torch.from_numpy(d.view("int32")).pin_memory()
+    learned_line = None
+    if not args.no_learned and rank == 0:
+        learned_line = learned_comparison(tc, g, stream)
     e2e_ms = []
     e2e_counts = None
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
@@ -347,6 +370,8 @@ def run_gpu(args):
         "step_ms": {"min": min(step_ms), "max": max(step_ms)},
         "timed_wall_s": wall,
     }
+    if learned_line is not None:
+        line["learned"] = learned_line
     if not args.no_batch:
         line["batched"] = batched_comparison(tc, torch, sh, stream, args.autotune_trials)
     if not args.no_cpu_baseline:

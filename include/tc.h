@@ -199,6 +199,50 @@ const char* tc_last_error(void);
 tc_status tc_census_csr_noalloc(uint32_t n, const uint64_t* d_off, const uint32_t* d_adj, void* stream,
                                 uint64_t* d_out16);
 
+/* ------------------------------------------------------------------ learned schedule
+ * A small network predicts, per vertex u, the SM cycles its pairs (u, v > u) cost the census
+ * (Fig. 5 step 2 unit); the plan then splits u's pairs into work items by that prediction
+ * (schedule TC_SCHED_LEARNED) instead of by the degree estimate.  It only reorders work: counts
+ * are the same either way.  Network: features log1p(out-degree, in-degree, degree, sum of
+ * neighbour degrees) -> 32 -> 32 -> 1 (tanh), FP16 weights, FP32 accumulation, output
+ * log(cycles); trained on the GPU with Adam on cycles measured by tc_census_profile. */
+typedef struct tc_costmodel tc_costmodel;
+uint32_t tc_costmodel_num_params(void);   /* 1249: W1[32][4] b1[32] W2[32][32] b2[32] W3[32] b3 */
+tc_status tc_costmodel_create(uint64_t seed, tc_costmodel** out);
+void tc_costmodel_destroy(tc_costmodel* c);
+/* FP32 master weights in the layout above (host arrays); set also refreshes the FP16 copy. */
+tc_status tc_costmodel_set_params(tc_costmodel* c, const float* host);
+tc_status tc_costmodel_get_params(const tc_costmodel* c, float* host);
+/* Input standardisation (x - mean) / std, target centring, and kappa = plan units per cycle. */
+tc_status tc_costmodel_set_norm(tc_costmodel* c, const float mean[4], const float std_[4], float target_mean,
+                                float kappa);
+tc_status tc_costmodel_get_norm(const tc_costmodel* c, float mean[4], float std_[4], float* target_mean, float* kappa);
+/* Fit the standardisation to training samples (device arrays) and set kappa. */
+tc_status tc_costmodel_fit_norm(tc_costmodel* c, const float* d_x4, const float* d_y, uint32_t count, float kappa,
+                                void* stream);
+/* Per-vertex features of a graph into d_feat4[4 n] (device, relabelled ids).  Asynchronous. */
+tc_status tc_graph_features(const tc_graph* g, void* stream, float* d_feat4);
+/* Training samples from a profiled census: every vertex split into CTA work items (degree
+ * above the graph's warp-tier threshold) with d_vcost > 0 contributes its
+ * features to d_x4 and log(cycles) to d_y (device, at most `capacity`, any order); *count
+ * receives the number written; est_sum / cycle_sum (may be NULL) the plain schedule's estimate
+ * and the measured cycles summed over those vertices (their ratio calibrates kappa). */
+tc_status tc_costmodel_samples(const tc_graph* g, const uint64_t* d_vcost, const float* d_feat4, uint32_t capacity,
+                               void* stream, float* d_x4, float* d_y, uint32_t* count, double* est_sum,
+                               double* cycle_sum);
+/* Mean squared error on log(cycles) and its gradient w.r.t. the parameters (host outputs,
+ * either may be NULL), computed with the FP16 weights and FP32 accumulation. */
+tc_status tc_costmodel_grad(tc_costmodel* c, const float* d_x4, const float* d_y, uint32_t count, void* stream,
+                            float* host_grad, float* host_loss);
+/* `steps` full-batch Adam steps (learning rate lr); *final_loss (may be NULL) after training. */
+tc_status tc_costmodel_train(tc_costmodel* c, const float* d_x4, const float* d_y, uint32_t count, uint32_t steps,
+                             float lr, void* stream, float* final_loss);
+/* Predicted cycles for count feature rows into d_out (device). */
+tc_status tc_costmodel_predict(const tc_costmodel* c, const float* d_x4, uint32_t count, void* stream, float* d_out);
+/* Compute the graph's features, predict each vertex's cost (cycles x kappa) and keep it for
+ * plans made with schedule TC_SCHED_LEARNED.  Synchronises `stream`. */
+tc_status tc_graph_attach_costmodel(tc_graph* g, const tc_costmodel* c, void* stream);
+
 /* The 64-entry tricode -> class table the kernels use (for inspection and tests). */
 void tc_tricode_table(uint8_t out[64]);
 

@@ -75,6 +75,24 @@ SIGNATURES = {
     "tc_batch_autotune": (ctypes.c_int, [_VP, _VP, _U32, _VP, ctypes.POINTER(ctypes.c_float)]),
     "tc_batch_stats": (ctypes.c_int, [_VP, ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
     "tc_batch_destroy": (None, [_VP]),
+    "tc_costmodel_num_params": (ctypes.c_uint32, []),
+    "tc_costmodel_create": (ctypes.c_int, [_U64, ctypes.POINTER(_VP)]),
+    "tc_costmodel_destroy": (None, [_VP]),
+    "tc_costmodel_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "tc_costmodel_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "tc_costmodel_set_norm": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                             ctypes.c_float, ctypes.c_float]),
+    "tc_costmodel_get_norm": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                             ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    "tc_costmodel_fit_norm": (ctypes.c_int, [_VP, _VP, _VP, _U32, ctypes.c_float, _VP]),
+    "tc_graph_features": (ctypes.c_int, [_VP, _VP, _VP]),
+    "tc_costmodel_samples": (ctypes.c_int, [_VP, _VP, _VP, _U32, _VP, _VP, _VP, ctypes.POINTER(_U32),
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "tc_costmodel_grad": (ctypes.c_int, [_VP, _VP, _VP, _U32, _VP, ctypes.POINTER(ctypes.c_float),
+                                         ctypes.POINTER(ctypes.c_float)]),
+    "tc_costmodel_train": (ctypes.c_int, [_VP, _VP, _VP, _U32, _U32, ctypes.c_float, _VP, ctypes.POINTER(ctypes.c_float)]),
+    "tc_costmodel_predict": (ctypes.c_int, [_VP, _VP, _U32, _VP, _VP]),
+    "tc_graph_attach_costmodel": (ctypes.c_int, [_VP, _VP, _VP]),
     "tc_graph_stats": (ctypes.c_int, [_VP, ctypes.POINTER(tc_graph_info)]),
     "tc_graph_device_csr": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     "tc_graph_export_csr": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -291,6 +309,107 @@ def tc_batch_stats(b: int):
 def tc_batch_destroy(b: int) -> None:
     if b:
         load().tc_batch_destroy(b)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def tc_costmodel_num_params() -> int:
+    return int(load().tc_costmodel_num_params())
+
+
+def tc_costmodel_create(seed: int = 0) -> int:
+    out = _VP()
+    _check(load().tc_costmodel_create(seed, ctypes.byref(out)), "tc_costmodel_create")
+    return out.value
+
+
+def tc_costmodel_destroy(c: int) -> None:
+    if c:
+        load().tc_costmodel_destroy(c)
+
+
+def tc_costmodel_set_params(c: int, params) -> None:
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != tc_costmodel_num_params():
+        raise ValueError("wrong parameter count")
+    _check(load().tc_costmodel_set_params(c, _fptr(a)), "tc_costmodel_set_params")
+
+
+def tc_costmodel_get_params(c: int) -> np.ndarray:
+    a = np.zeros(tc_costmodel_num_params(), np.float32)
+    _check(load().tc_costmodel_get_params(c, _fptr(a)), "tc_costmodel_get_params")
+    return a
+
+
+def tc_costmodel_set_norm(c: int, mean, std, target_mean: float, kappa: float) -> None:
+    m = np.ascontiguousarray(mean, np.float32)
+    sd = np.ascontiguousarray(std, np.float32)
+    _check(load().tc_costmodel_set_norm(c, _fptr(m), _fptr(sd), float(target_mean), float(kappa)),
+           "tc_costmodel_set_norm")
+
+
+def tc_costmodel_get_norm(c: int):
+    m = np.zeros(4, np.float32)
+    sd = np.zeros(4, np.float32)
+    tm, kp = ctypes.c_float(), ctypes.c_float()
+    _check(load().tc_costmodel_get_norm(c, _fptr(m), _fptr(sd), ctypes.byref(tm), ctypes.byref(kp)),
+           "tc_costmodel_get_norm")
+    return m, sd, float(tm.value), float(kp.value)
+
+
+def tc_costmodel_fit_norm(c: int, d_x4, d_y, count: int, kappa: float, stream=None) -> None:
+    px, _, k1 = _buffer(d_x4, np.float32)
+    py, _, k2 = _buffer(d_y, np.float32)
+    _check(load().tc_costmodel_fit_norm(c, px, py, count, float(kappa), _stream_handle(stream)), "tc_costmodel_fit_norm")
+
+
+def tc_graph_features(g: int, d_feat4, stream=None) -> None:
+    p, dev, keep = _buffer(d_feat4, np.float32)
+    _check(load().tc_graph_features(g, _stream_handle(stream), p), "tc_graph_features")
+
+
+def tc_costmodel_samples(g: int, d_vcost, d_feat4, d_x4, d_y, capacity: int, stream=None):
+    """-> (count, plain estimate sum, measured cycle sum)"""
+    pv, _, k1 = _buffer(d_vcost, np.uint64)
+    pf, _, k2 = _buffer(d_feat4, np.float32)
+    px, _, k3 = _buffer(d_x4, np.float32)
+    py, _, k4 = _buffer(d_y, np.float32)
+    cnt = _U32()
+    es, cs = ctypes.c_double(), ctypes.c_double()
+    _check(load().tc_costmodel_samples(g, pv, pf, capacity, _stream_handle(stream), px, py, ctypes.byref(cnt),
+                                       ctypes.byref(es), ctypes.byref(cs)), "tc_costmodel_samples")
+    return int(cnt.value), float(es.value), float(cs.value)
+
+
+def tc_costmodel_grad(c: int, d_x4, d_y, count: int, stream=None):
+    px, _, k1 = _buffer(d_x4, np.float32)
+    py, _, k2 = _buffer(d_y, np.float32)
+    g = np.zeros(tc_costmodel_num_params(), np.float32)
+    loss = ctypes.c_float()
+    _check(load().tc_costmodel_grad(c, px, py, count, _stream_handle(stream), _fptr(g), ctypes.byref(loss)),
+           "tc_costmodel_grad")
+    return g, float(loss.value)
+
+
+def tc_costmodel_train(c: int, d_x4, d_y, count: int, steps: int, lr: float, stream=None) -> float:
+    px, _, k1 = _buffer(d_x4, np.float32)
+    py, _, k2 = _buffer(d_y, np.float32)
+    loss = ctypes.c_float()
+    _check(load().tc_costmodel_train(c, px, py, count, steps, float(lr), _stream_handle(stream), ctypes.byref(loss)),
+           "tc_costmodel_train")
+    return float(loss.value)
+
+
+def tc_costmodel_predict(c: int, d_x4, count: int, d_out, stream=None) -> None:
+    px, _, k1 = _buffer(d_x4, np.float32)
+    po, _, k2 = _buffer(d_out, np.float32)
+    _check(load().tc_costmodel_predict(c, px, count, _stream_handle(stream), po), "tc_costmodel_predict")
+
+
+def tc_graph_attach_costmodel(g: int, c: int, stream=None) -> None:
+    _check(load().tc_graph_attach_costmodel(g, c, _stream_handle(stream)), "tc_graph_attach_costmodel")
 
 
 def tc_graph_stats(g: int) -> dict:
