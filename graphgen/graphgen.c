@@ -53,23 +53,60 @@ enum { TAG_RMAT = 0x524d4154, TAG_PERM = 0x5045524d, TAG_RECIP = 0x52454350,
 
 /* ---------------------------------------------------------------- sorting (keys) */
 /* LSD radix sort of 64-bit keys with 16-bit digits; digits that are constant over the
- * whole array are skipped.  Returns a pointer to whichever buffer holds the result. */
+ * whole array are skipped.  Each thread histograms and scatters its own contiguous block,
+ * in thread order, so every pass is stable.  Returns a pointer to whichever buffer holds
+ * the result. */
 static uint64_t* radix_sort_u64(uint64_t* a, uint64_t* tmp, uint64_t cnt) {
-    size_t* hist = (size_t*)malloc(sizeof(size_t) * 65536);
+    int T = 1;
+#ifdef _OPENMP
+    /* one thread when already inside a parallel region (nested regions get one thread) */
+    T = (cnt >= (1u << 20) && !omp_in_parallel()) ? omp_get_max_threads() : 1;
+#endif
+    size_t* hist = (size_t*)malloc(sizeof(size_t) * 65536 * (size_t)T);
     for (int pass = 0; pass < 4; ++pass) {
         int sh = pass * 16;
-        memset(hist, 0, sizeof(size_t) * 65536);
-        for (uint64_t i = 0; i < cnt; ++i) hist[(a[i] >> sh) & 0xffff]++;
+        memset(hist, 0, sizeof(size_t) * 65536 * (size_t)T);
+#pragma omp parallel num_threads(T)
+        {
+            int t = 0;
+#ifdef _OPENMP
+            t = omp_get_thread_num();
+#endif
+            uint64_t b0 = cnt * (uint64_t)t / (uint64_t)T, b1 = cnt * (uint64_t)(t + 1) / (uint64_t)T;
+            size_t* h = hist + 65536 * (size_t)t;
+            for (uint64_t i = b0; i < b1; ++i) h[(a[i] >> sh) & 0xffff]++;
+        }
         int only = 0;
-        for (int d = 0; d < 65536; ++d) if (hist[d] == cnt) { only = 1; break; }
+        for (int d = 0; d < 65536 && !only; ++d) {
+            size_t tot = 0;
+            for (int t = 0; t < T; ++t) tot += hist[65536 * (size_t)t + d];
+            if (tot == cnt) only = 1;
+        }
         if (only) continue;
         size_t s = 0;
-        for (int d = 0; d < 65536; ++d) { size_t h = hist[d]; hist[d] = s; s += h; }
-        for (uint64_t i = 0; i < cnt; ++i) tmp[hist[(a[i] >> sh) & 0xffff]++] = a[i];
+        for (int d = 0; d < 65536; ++d)
+            for (int t = 0; t < T; ++t) { size_t* h = &hist[65536 * (size_t)t + d]; size_t c = *h; *h = s; s += c; }
+#pragma omp parallel num_threads(T)
+        {
+            int t = 0;
+#ifdef _OPENMP
+            t = omp_get_thread_num();
+#endif
+            uint64_t b0 = cnt * (uint64_t)t / (uint64_t)T, b1 = cnt * (uint64_t)(t + 1) / (uint64_t)T;
+            size_t* h = hist + 65536 * (size_t)t;
+            for (uint64_t i = b0; i < b1; ++i) tmp[h[(a[i] >> sh) & 0xffff]++] = a[i];
+        }
         uint64_t* t = a; a = tmp; tmp = t;
     }
     free(hist);
     return a;
+}
+
+/* Keep the entries with flag set, in order (flag[i] in {0, 1}); returns the count. */
+static uint64_t compact_flagged(uint64_t* k, const uint8_t* flag, uint64_t cnt) {
+    uint64_t o = 0;
+    for (uint64_t i = 0; i < cnt; ++i) if (flag[i]) k[o++] = k[i];
+    return o;
 }
 
 /* Drop loops (already excluded by caller) and duplicates from sorted keys; returns count */
@@ -96,12 +133,17 @@ static int64_t finish_arcs(uint64_t* keys, uint64_t cnt, double recip, uint64_t 
     uint64_t m = unique_sorted(s, cnt);
     /* reciprocation: decisions depend only on (seed, index in sorted clean list) */
     uint64_t rk = stream_key(seed, TAG_RECIP);
-    uint64_t add = 0;
-    for (uint64_t i = 0; i < m; ++i) {
+    uint8_t* addf = (uint8_t*)malloc(m ? m : 1);
+    if (!addf) { free(tmp); return -1; }
+#pragma omp parallel for schedule(static) if (m >= (1u << 16))
+    for (int64_t i = 0; i < (int64_t)m; ++i) {
         uint64_t x = s[i] >> 32, y = s[i] & 0xffffffffull;
         uint64_t rev = (y << 32) | x;
-        if (recip > 0.0 && u01(ctr_rand(rk, i)) < recip && !key_present(s, m, rev)) other[add++] = rev;
+        other[i] = rev;
+        addf[i] = recip > 0.0 && u01(ctr_rand(rk, (uint64_t)i)) < recip && !key_present(s, m, rev);
     }
+    uint64_t add = compact_flagged(other, addf, m);
+    free(addf);
     uint64_t tot = m + add;
     uint64_t* all = (uint64_t*)malloc(sizeof(uint64_t) * (tot ? tot : 1));
     uint64_t* all_tmp = (uint64_t*)malloc(sizeof(uint64_t) * (tot ? tot : 1));
@@ -170,7 +212,7 @@ int64_t gg_rmat(uint32_t scale, uint32_t edge_factor, double a, double b, double
         keys[i] = (s << 32) | d;
         keep[i] = (s != d);
     }
-    for (uint64_t i = 0; i < draws; ++i) if (keep[i]) keys[kept++] = keys[i];
+    kept = (int64_t)compact_flagged(keys, keep, draws);
     free(keep); free(perm);
     int64_t r = finish_arcs(keys, (uint64_t)kept, recip, seed, src_out, dst_out);
     free(keys);
@@ -198,8 +240,11 @@ int64_t gg_chung_lu(uint32_t n, double mean_deg, double gamma, double recip, uin
     double so = 0.0, si = 0.0;
     for (uint32_t j = 0; j < n; ++j) { so += wout[j]; cout_[j] = so; si += wout[perm[j]]; cin[j] = si; }
     uint64_t ak = stream_key(gseed, TAG_CLA);
-    uint64_t kept = 0;
-    for (uint64_t i = 0; i < draws; ++i) {
+    uint8_t* keep = (uint8_t*)malloc(draws ? draws : 1);
+    if (!keep) { free(wout); free(cout_); free(cin); free(perm); free(keys); return -1; }
+#pragma omp parallel for schedule(static) if (draws >= (1u << 16))
+    for (int64_t ii = 0; ii < (int64_t)draws; ++ii) {
+        uint64_t i = (uint64_t)ii;
         double x = u01(ctr_rand(ak, 2 * i)) * so, y = u01(ctr_rand(ak, 2 * i + 1)) * si;
         uint32_t lo = 0, hi = n - 1;
         while (lo < hi) { uint32_t mid = (lo + hi) >> 1; if (cout_[mid] <= x) lo = mid + 1; else hi = mid; }
@@ -207,8 +252,11 @@ int64_t gg_chung_lu(uint32_t n, double mean_deg, double gamma, double recip, uin
         lo = 0; hi = n - 1;
         while (lo < hi) { uint32_t mid = (lo + hi) >> 1; if (cin[mid] <= y) lo = mid + 1; else hi = mid; }
         uint32_t d = lo;
-        if (s != d) keys[kept++] = ((uint64_t)s << 32) | d;
+        keys[i] = ((uint64_t)s << 32) | d;
+        keep[i] = (s != d);
     }
+    uint64_t kept = compact_flagged(keys, keep, draws);
+    free(keep);
     free(wout); free(cout_); free(cin); free(perm);
     int64_t r = finish_arcs(keys, kept, recip, gseed, src_out, dst_out);
     free(keys);
