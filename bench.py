@@ -47,6 +47,10 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the 4096-graph batched comparison")
     p.add_argument("--autotune-trials", type=int, default=12)
     p.add_argument("--no-learned", action="store_true", help="skip the learned-schedule comparison")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) run")
+    p.add_argument("--serve-seconds", type=float, default=20.0, help="measured seconds per serving arm")
+    p.add_argument("--serve-warmup", type=float, default=5.0, help="unmeasured seconds before them")
+    p.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
     return p.parse_args()
 
 
@@ -246,23 +250,120 @@ def batched_comparison(tc, torch, sh, st, trials):
             "counts_identical": same_default and same_tuned}
 
 
-def learned_comparison(tc, g, stream):
+def learned_comparison(tc, g, stream, model, info):
     """Cost model trained on R-MAT scales 18-22 (seeds 18-22) from cycles the plain census
     measures, attached to the bench graph: census time with the plain and the learned schedule
     (identical counts required) and the held-out cost-prediction error of both."""
     from paper_1209_6308_gb300 import learned
-    model, info = learned.train_cost_model(scales=(18, 19, 20, 21, 22), steps=800, stream=stream.cuda_stream)
-    try:
-        learned.attach(model, g, stream=stream.cuda_stream)
-        plain_ms, plain_c = learned.census_ms(g, learned.PLAIN, stream)
-        learned_ms, learned_c = learned.census_ms(g, learned.LEARNED, stream)
-        q = learned.prediction_quality(model, g, stream=stream.cuda_stream)
-    finally:
-        tc.tc_costmodel_destroy(model)
+    learned.attach(model, g, stream=stream.cuda_stream)
+    plain_ms, plain_c = learned.census_ms(g, learned.PLAIN, stream)
+    learned_ms, learned_c = learned.census_ms(g, learned.LEARNED, stream)
+    q = learned.prediction_quality(model, g, stream=stream.cuda_stream)
     return {"training": info, "plain_ms": plain_ms, "learned_ms": learned_ms,
             "speedup": plain_ms / learned_ms, "counts_identical": plain_c == learned_c,
             "heldout_rms_log_cycle_error": {"model": q["rms_log_err_model"], "degree": q["rms_log_err_degree"],
                                             "vertices": q["vertices"]}}
+
+
+SERVE_POOL = "pool_chunglu16_n1e3-1e7_d12+rmat16-22_ef16"
+
+
+def serving_pool():
+    """Resident graphs of the serving workload: 16 directed Chung-Lu graphs (n log-uniform in
+    [1e3, 1e7], exponent 2.1, mean degree 12, 10% reciprocated, seed 5, graph index i) and R-MAT
+    scales 16-22 (edge factor 16, 20% reciprocated, seed 100 + scale)."""
+    import graphgen
+    sizes = graphgen.loguniform_sizes(16, 1e3, 1e7, 5)
+    pool = [(f"chunglu_n{int(n)}", graphgen.chung_lu(int(n), 12.0, 2.1, 0.1, 5, i)) for i, n in enumerate(sizes)]
+    pool += [(f"rmat{sc}", graphgen.rmat(sc, 16, 0.2, 100 + sc)) for sc in range(16, 23)]
+    return pool
+
+
+def serve_arm(tc, gs, arcs, census_opts, rate, seconds, warmup, seed):
+    """Open-loop Poisson client (rate requests/s, graph i chosen with probability proportional
+    to 1/arcs_i so every graph draws the same arc volume) against one server; latency is
+    result-complete minus submit on the server's clock.  Every result is checked against the
+    graph's standalone census."""
+    import threading
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    total = int(rate * (warmup + seconds))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, total))
+    w = 1.0 / np.asarray(arcs, dtype=np.float64)
+    choice = rng.choice(len(gs), total, p=w / w.sum())
+    results, done = [], threading.Event()
+    with tc.Server({"quantum_us": 1000, "lanes": 2}, census_opts) as srv:
+        ids = [srv.add(g) for g in gs]
+
+        def collector():
+            while len(results) < total and not done.is_set():
+                results.extend(srv.poll(4096, timeout_ms=50))
+
+        th = threading.Thread(target=collector, daemon=True)
+        th.start()
+        rid_graph, submit_lag = {}, []
+        t0 = time.perf_counter()
+        for k in range(total):
+            due = t0 + arrivals[k]
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 2e-3:
+                    time.sleep(due - now - 1e-3)
+            submit_lag.append(time.perf_counter() - due)
+            rid_graph[srv.submit(ids[choice[k]])] = (k, int(choice[k]))
+        srv.drain(600000)
+        th.join(timeout=60)
+        done.set()
+        stats = srv.stats()
+    meas = [r for r in results if arrivals[rid_graph[r.id][0]] >= warmup]
+    lat = np.array([(r.done_ns - r.submit_ns) * 1e-6 for r in meas])
+    t_first = min(r.submit_ns for r in meas)
+    t_last = max(r.done_ns for r in meas)
+    arcs_done = sum(arcs[rid_graph[r.id][1]] for r in meas)
+    return {"requests": len(meas), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "arcs_per_s": arcs_done / ((t_last - t_first) * 1e-9),
+            "offered_arcs_per_s": rate * float(np.sum(w / w.sum() * np.asarray(arcs))),
+            "achieved_rate": len(meas) / ((t_last - t_first) * 1e-9),
+            "gpu_busy_frac": stats["gpu_ms"] * 1e-3 / (time.perf_counter() - t0),
+            "waves": stats["waves"], "slices_per_wave": stats["slices"] / max(stats["waves"], 1),
+            "mean_waves_per_request": float(np.mean([r.waves for r in results])),
+            "submit_lag_p99_ms": float(np.percentile(submit_lag, 99)) * 1e3,
+            "errors": int(sum(1 for r in results if r.status != 0)), "completed": len(results)}, results, rid_graph
+
+
+def serving_comparison(tc, torch, sh, model, args):
+    """Serving workload with the plain and the learned schedule: p50/p99 latency and arcs/s."""
+    from paper_1209_6308_gb300 import learned
+    t0 = time.perf_counter()
+    pool = serving_pool()
+    gen_s = time.perf_counter() - t0
+    gs = [tc.Graph.from_arcs(n, s, d, stream=sh, options=learned.PLAIN) for (_, (n, s, d)) in pool]
+    arcs = [len(s) for (_, (_, s, _)) in pool]
+    want = [g.census(stream=sh, options=learned.PLAIN) for g in gs]
+    out = {"workload": SERVE_POOL + f"_poisson{int(args.serve_rate)}_seed5", "graphs": len(gs),
+           "pool_arcs": int(sum(arcs)), "rate_per_s": args.serve_rate, "measured_s": args.serve_seconds,
+           "warmup_s": args.serve_warmup, "quantum_us": 1000, "lanes": 2, "pool_generation_s": gen_s,
+           "selection": "graph i with probability proportional to 1/arcs_i"}
+    try:
+        arms = [("plain", learned.PLAIN)]
+        if model is not None:
+            for g in gs:
+                learned.attach(model, g, stream=sh)
+            arms.append(("learned", learned.LEARNED))
+        exact = True
+        for name, opts in arms:
+            m, res, rid_graph = serve_arm(tc, gs, arcs, opts, args.serve_rate, args.serve_seconds,
+                                          args.serve_warmup, 5)
+            exact &= all(r.census() == want[rid_graph[r.id][1]] for r in res)
+            out[name] = m
+        out["counts_identical_to_standalone"] = exact
+    finally:
+        for g in gs:
+            g.close()
+    return out
 
 
 def run_gpu(args):
@@ -324,8 +425,11 @@ def run_gpu(args):
     src_pin = torch.from_numpy(s.view("int32")).pin_memory()
     dst_pin = torch.from_numpy(d.view("int32")).pin_memory()
     learned_line = None
+    model = None
     if not args.no_learned and rank == 0:
-        learned_line = learned_comparison(tc, g, stream)
+        from paper_1209_6308_gb300 import learned
+        model, minfo = learned.train_cost_model(scales=(18, 19, 20, 21, 22), steps=800, stream=sh)
+        learned_line = learned_comparison(tc, g, stream, model, minfo)
     e2e_ms = []
     e2e_counts = None
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
@@ -344,6 +448,11 @@ def run_gpu(args):
         if dist:
             dist.destroy_process_group()
         return 0
+    serve_line = None
+    if not args.no_serve:
+        serve_line = serving_comparison(tc, torch, sh, model, args)
+    if model is not None:
+        tc.tc_costmodel_destroy(model)
 
     peak, peak_kind = measured_peak()
     bytes_alg = info["bytes_alg"]
@@ -372,6 +481,8 @@ def run_gpu(args):
     }
     if learned_line is not None:
         line["learned"] = learned_line
+    if serve_line is not None:
+        line["serving"] = serve_line
     if not args.no_batch:
         line["batched"] = batched_comparison(tc, torch, sh, stream, args.autotune_trials)
     if not args.no_cpu_baseline:

@@ -243,6 +243,84 @@ tc_status tc_costmodel_predict(const tc_costmodel* c, const float* d_x4, uint32_
  * plans made with schedule TC_SCHED_LEARNED.  Synchronises `stream`. */
 tc_status tc_graph_attach_costmodel(tc_graph* g, const tc_costmodel* c, void* stream);
 
+/* ------------------------------------------------------------------ serving
+ * A census server keeps graphs resident on the GPU and answers census requests on them (the
+ * paper's monitoring use runs the census repeatedly at fixed intervals, Sec. 3) with
+ * continuous batching: an engine thread runs each request as slices of its work items
+ * (Fig. 5 step 2 pairs), up to 32 slices of different requests per launch ("wave") of the
+ * census kernel, each wave sized to a target device time.  New requests join the next wave;
+ * shortest remaining work goes first, and requests older than starve_ms before all others.
+ * Counts are exactly those of tc_census.
+ *
+ * Thread safety: submit, poll, drain and stats may be called from any thread; add/remove
+ * from any thread.  A registered graph must not be destroyed before tc_server_remove_graph,
+ * and the census options of the server apply to every graph (a TC_SCHED_LEARNED server needs
+ * a cost model attached to each graph before it is added). */
+typedef struct tc_server tc_server;
+
+typedef struct {
+    tc_options census;        /* kernel options shared by every resident graph */
+    uint64_t budget_bytes;    /* cap on resident graph bytes (0 = 90% of device memory) */
+    uint32_t max_active;      /* requests in execution at once, one output slot each (0 = 1024) */
+    uint32_t max_pending;     /* queued requests beyond which submit returns TC_ERR_BUSY (0 = 65536) */
+    uint32_t quantum_us;      /* target device time of one wave (0 = 1000) */
+    uint32_t lanes;           /* CUDA streams waves are issued on, 1..4 (0 = 2) */
+    uint32_t starve_ms;       /* age after which a request is served before all younger ones (0 = 50) */
+    uint32_t reserved[9];
+} tc_server_options;
+
+typedef struct {
+    uint64_t id;              /* the id tc_server_submit returned */
+    uint32_t graph;           /* the graph id of the request */
+    int32_t status;           /* tc_status of the request (TC_OK, or TC_ERR_CUDA if its wave failed) */
+    uint64_t counts[16];      /* census in the order above; counts[0] = 003 mod 2^64 */
+    tc_u128 c003;             /* the null count in full */
+    uint64_t submit_ns;       /* tc_server_now_ns() clock: submitted, */
+    uint64_t start_ns;        /*   first slice launched, */
+    uint64_t done_ns;         /*   result seen complete by the engine */
+    uint32_t waves;           /* waves the request took part in */
+    uint32_t lane;            /* stream index it ran on */
+} tc_serve_result;
+
+typedef struct {
+    uint64_t submitted, completed, refused;   /* refused: graphs turned away by admission */
+    uint64_t waves, slices;
+    uint64_t resident_bytes, budget_bytes;
+    uint32_t graphs, active, pending, inflight_waves;
+    double gpu_ms;            /* summed device time of the waves (CUDA events) */
+    double ns_per_unit;       /* calibrated device ns per element unit of the slice cost model */
+    int32_t error;            /* first engine error (tc_status), 0 if none */
+    uint32_t reserved[7];
+} tc_server_info;
+
+/* Monotonic clock (ns) of the result timestamps. */
+uint64_t tc_server_now_ns(void);
+/* Start a server on the current device (opt may be NULL).  Starts the engine thread. */
+tc_status tc_server_create(const tc_server_options* opt, tc_server** out);
+/* Register a built graph: makes its work plan under the server's options, copies the plan and
+ * computes each work item's cost on `stream` (synchronised).  Admission: TC_ERR_OOM, with
+ * nothing registered, if the server's resident bytes (CSR, relabelling and plan copy of every
+ * registered graph) would exceed budget_bytes.  *graph_id receives the id requests name. */
+tc_status tc_server_add_graph(tc_server* s, tc_graph* g, void* stream, uint32_t* graph_id);
+/* Unregister a graph (TC_ERR_BUSY while requests for it are queued or running). */
+tc_status tc_server_remove_graph(tc_server* s, uint32_t graph_id);
+/* Queue a census of graph graph_id; *request_id (may be NULL) receives its id.  TC_ERR_ARG for
+ * an unknown graph, TC_ERR_BUSY when max_pending requests are queued.  Never blocks on the GPU. */
+tc_status tc_server_submit(tc_server* s, uint32_t graph_id, uint64_t* request_id);
+/* Up to `max` finished results, waiting at most timeout_ms for the first; *count = number
+ * written (0 on timeout).  Each result is returned once. */
+tc_status tc_server_poll(tc_server* s, tc_serve_result* out, uint32_t max, uint32_t timeout_ms, uint32_t* count);
+/* Wait, at most timeout_ms, until every submitted request has finished (TC_ERR_TIMEOUT if
+ * not); returns the first engine error if one occurred.  Results stay queued for poll. */
+tc_status tc_server_drain(tc_server* s, uint32_t timeout_ms);
+tc_status tc_server_stats(tc_server* s, tc_server_info* info);
+/* Total cost units (element units) of a registered graph's census and its work counts. */
+tc_status tc_server_graph_units(tc_server* s, uint32_t graph_id, uint64_t* units, uint32_t* n_items,
+                                uint32_t* n_blocks);
+/* Stop the engine: queued requests that have not started are dropped, started ones finish;
+ * then free the server (registered graphs are not destroyed). */
+void tc_server_destroy(tc_server* s);
+
 /* The 64-entry tricode -> class table the kernels use (for inspection and tests). */
 void tc_tricode_table(uint8_t out[64]);
 

@@ -54,6 +54,34 @@ class tc_graph_info(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class tc_server_options(ctypes.Structure):
+    _fields_ = [("census", tc_options), ("budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_uint32),
+                ("max_pending", ctypes.c_uint32), ("quantum_us", ctypes.c_uint32), ("lanes", ctypes.c_uint32),
+                ("starve_ms", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 9)]
+
+
+class tc_serve_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("graph", ctypes.c_uint32), ("status", ctypes.c_int32),
+                ("counts", ctypes.c_uint64 * 16), ("c003", tc_u128), ("submit_ns", ctypes.c_uint64),
+                ("start_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64), ("waves", ctypes.c_uint32),
+                ("lane", ctypes.c_uint32)]
+
+    def census(self) -> list:
+        return [self.c003.value()] + [int(self.counts[t]) for t in range(1, 16)]
+
+
+class tc_server_info(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("refused", ctypes.c_uint64),
+                ("waves", ctypes.c_uint64), ("slices", ctypes.c_uint64), ("resident_bytes", ctypes.c_uint64),
+                ("budget_bytes", ctypes.c_uint64), ("graphs", ctypes.c_uint32), ("active", ctypes.c_uint32),
+                ("pending", ctypes.c_uint32), ("inflight_waves", ctypes.c_uint32), ("gpu_ms", ctypes.c_double),
+                ("ns_per_unit", ctypes.c_double), ("error", ctypes.c_int32), ("reserved", ctypes.c_uint32 * 7)]
+
+    def as_dict(self) -> dict:
+        return {k: (float(getattr(self, k)) if k in ("gpu_ms", "ns_per_unit") else int(getattr(self, k)))
+                for k, _ in self._fields_ if k != "reserved"}
+
+
 _lib = None
 _VP, _U32, _U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
 
@@ -99,6 +127,17 @@ SIGNATURES = {
     "tc_graph_destroy": (None, [_VP]),
     "tc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "tc_last_error": (ctypes.c_char_p, []),
+    "tc_server_now_ns": (_U64, []),
+    "tc_server_create": (ctypes.c_int, [ctypes.POINTER(tc_server_options), ctypes.POINTER(_VP)]),
+    "tc_server_add_graph": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(_U32)]),
+    "tc_server_remove_graph": (ctypes.c_int, [_VP, _U32]),
+    "tc_server_submit": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(_U64)]),
+    "tc_server_poll": (ctypes.c_int, [_VP, ctypes.POINTER(tc_serve_result), _U32, _U32, ctypes.POINTER(_U32)]),
+    "tc_server_drain": (ctypes.c_int, [_VP, _U32]),
+    "tc_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(tc_server_info)]),
+    "tc_server_graph_units": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(_U64), ctypes.POINTER(_U32),
+                                             ctypes.POINTER(_U32)]),
+    "tc_server_destroy": (None, [_VP]),
     "tc_tricode_table": (None, [ctypes.POINTER(ctypes.c_uint8)]),
 }
 
@@ -445,6 +484,109 @@ def tc_tricode_table() -> np.ndarray:
     t = np.zeros(64, dtype=np.uint8)
     load().tc_tricode_table(t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
     return t
+
+
+def tc_server_now_ns() -> int:
+    return int(load().tc_server_now_ns())
+
+
+def tc_server_create(options=None, census=None) -> int:
+    """Start a census server; `options` sets tc_server_options fields, `census` its tc_options."""
+    o = tc_server_options()
+    for k, v in dict(options or {}).items():
+        setattr(o, k, int(v))
+    for k, v in dict(census or {}).items():
+        setattr(o.census, k, int(v))
+    out = _VP()
+    _check(load().tc_server_create(ctypes.byref(o), ctypes.byref(out)), "tc_server_create")
+    return out.value
+
+
+def tc_server_add_graph(s: int, g: int, stream=None) -> int:
+    gid = _U32()
+    _check(load().tc_server_add_graph(s, g, _stream_handle(stream), ctypes.byref(gid)), "tc_server_add_graph")
+    return int(gid.value)
+
+
+def tc_server_remove_graph(s: int, graph_id: int) -> None:
+    _check(load().tc_server_remove_graph(s, graph_id), "tc_server_remove_graph")
+
+
+def tc_server_submit(s: int, graph_id: int) -> int:
+    rid = _U64()
+    _check(load().tc_server_submit(s, graph_id, ctypes.byref(rid)), "tc_server_submit")
+    return int(rid.value)
+
+
+def tc_server_poll(s: int, max_results: int = 256, timeout_ms: int = 0) -> list:
+    buf = (tc_serve_result * max(max_results, 1))()
+    cnt = _U32()
+    _check(load().tc_server_poll(s, buf, max_results, timeout_ms, ctypes.byref(cnt)), "tc_server_poll")
+    return [buf[i] for i in range(cnt.value)]
+
+
+def tc_server_drain(s: int, timeout_ms: int = 60000) -> None:
+    _check(load().tc_server_drain(s, timeout_ms), "tc_server_drain")
+
+
+def tc_server_stats(s: int) -> dict:
+    info = tc_server_info()
+    _check(load().tc_server_stats(s, ctypes.byref(info)), "tc_server_stats")
+    return info.as_dict()
+
+
+def tc_server_graph_units(s: int, graph_id: int):
+    u, ni, nb = _U64(), _U32(), _U32()
+    _check(load().tc_server_graph_units(s, graph_id, ctypes.byref(u), ctypes.byref(ni), ctypes.byref(nb)),
+           "tc_server_graph_units")
+    return int(u.value), int(ni.value), int(nb.value)
+
+
+def tc_server_destroy(s: int) -> None:
+    if s:
+        load().tc_server_destroy(s)
+
+
+class Server:
+    """Owning wrapper around a tc_server handle (continuous-batching census serving)."""
+
+    def __init__(self, options=None, census=None):
+        self.handle = tc_server_create(options, census)
+
+    def add(self, g, stream=None) -> int:
+        return tc_server_add_graph(self.handle, g.handle if isinstance(g, Graph) else g, stream)
+
+    def remove(self, graph_id: int) -> None:
+        tc_server_remove_graph(self.handle, graph_id)
+
+    def submit(self, graph_id: int) -> int:
+        return tc_server_submit(self.handle, graph_id)
+
+    def poll(self, max_results: int = 256, timeout_ms: int = 0) -> list:
+        return tc_server_poll(self.handle, max_results, timeout_ms)
+
+    def drain(self, timeout_ms: int = 60000) -> None:
+        tc_server_drain(self.handle, timeout_ms)
+
+    def stats(self) -> dict:
+        return tc_server_stats(self.handle)
+
+    def close(self):
+        tc_server_destroy(self.handle)
+        self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self.handle:
+                self.close()
+        except Exception:
+            pass
 
 
 class Graph:

@@ -65,7 +65,23 @@ struct Params {
     const GraphDev* graphs;
     const uint4* wblocks;
     uint32_t n_wblocks;
+    // wave launch (serving): request r's items and warp-tier blocks, counts to out[16 r ..]
+    const WaveReq* reqs;
+    uint32_t n_reqs;
 };
+
+enum { kModeSingle = 0, kModeBatch = 1, kModeWave = 2 };
+
+// index r of the last request whose prefix is <= i (prefixes ascend, pre[0] = 0)
+template <typename F>
+__device__ __forceinline__ uint32_t wave_find(uint32_t count, uint32_t i, F pre) {
+    uint32_t lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre(mid) <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -234,7 +250,7 @@ __device__ __forceinline__ void flush_graph(Counts& k, int lane, unsigned long l
     k.racc = 0;
 }
 
-template <int ALGO, bool BATCH = false>
+template <int ALGO, int MODE = kModeSingle>
 __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t chunk = P.chunk;
@@ -250,10 +266,14 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     unsigned long long* sC = reinterpret_cast<unsigned long long*>(sCur + kMaxItemPairs);  // [16]
     uint8_t* sT = reinterpret_cast<uint8_t*>(sC + 16);                                // [64]
     __shared__ uint32_t s_item, s_next;
+    __shared__ WaveReq sReq[MODE == kModeWave ? kMaxWave : 1];
+    constexpr bool MULTI = MODE != kModeSingle;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid < 16) sC[tid] = 0;
     if (tid < 64) sT[tid] = d_tricode_class[tid];
+    if (MODE == kModeWave)
+        for (uint32_t i = tid; i < P.n_reqs; i += kThreads) sReq[i] = P.reqs[i];
     if (P.phase && tid == 0) P.phase[3 * blockIdx.x] = global_ns();
     __syncthreads();
 
@@ -272,12 +292,12 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     auto use_graph = [&](uint32_t gi) {
         if (cur_graph != 0xffffffffu) flush_graph(cnt, lane, gout);
         cur_graph = gi;
-        const GraphDev G = P.graphs[gi];
+        const GraphDev G = MODE == kModeWave ? sReq[gi].g : P.graphs[gi];
         n = G.n;
         off = G.off;
         adj = G.adj;
         upv = G.up;
-        gout = P.out + 16ull * gi;
+        gout = MODE == kModeWave ? sReq[gi].out : P.out + 16ull * gi;
     };
 
     // ---------------------------------------------------------------- CTA items
@@ -286,8 +306,15 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
         __syncthreads();
         const uint32_t it = s_item;
         if (it >= P.n_items) break;
-        const Item w = P.items[it];
-        if (BATCH && w.pad != cur_graph) use_graph(w.pad);
+        Item w;
+        if (MODE == kModeWave) {
+            const uint32_t r = wave_find(P.n_reqs, it, [&](uint32_t q) { return sReq[q].item_pre; });
+            w = sReq[r].items[it - sReq[r].item_pre];
+            if (r != cur_graph) use_graph(r);
+        } else {
+            w = P.items[it];
+            if (MODE == kModeBatch && w.pad != cur_graph) use_graph(w.pad);
+        }
         const long long t_item = clock64();
         const uint32_t u = w.u;
         const uint64_t ubase = off[u];
@@ -439,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
             }
             __syncthreads();   // all warps are done with this chunk before it is replaced
         }
-        if (!BATCH && P.vcost && tid == 0) atomicAdd(&P.vcost[u], (unsigned long long)(clock64() - t_item));
+        if (!MULTI && P.vcost && tid == 0) atomicAdd(&P.vcost[u], (unsigned long long)(clock64() - t_item));
     }
     if (P.phase && tid == 0) P.phase[3 * blockIdx.x + 1] = global_ns();
 
@@ -447,7 +474,16 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     uint32_t* wA = reinterpret_cast<uint32_t*>(smem) + warp * P.warp_max;
     for (;;) {
         uint32_t u0, u1;
-        if (BATCH) {
+        if (MODE == kModeWave) {
+            uint32_t b = 0;
+            if (lane == 0) b = atomicAdd(&P.ctr[1], 1u);
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (b >= P.n_wblocks) break;
+            const uint32_t r = wave_find(P.n_reqs, b, [&](uint32_t q) { return sReq[q].block_pre; });
+            if (r != cur_graph) use_graph(r);
+            u0 = sReq[r].warp_begin + 32u * (b - sReq[r].block_pre);
+            u1 = min(u0 + 32u, sReq[r].warp_end);
+        } else if (MODE == kModeBatch) {
             uint32_t b = 0;
             if (lane == 0) b = atomicAdd(&P.ctr[1], 1u);
             b = __shfl_sync(0xffffffffu, b, 0);
@@ -529,12 +565,12 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                     pair_fold(cnt, pa, lane, duv, cuv, sT, suf, n - du - dv);
                 }
             }
-            if (!BATCH && P.vcost && lane == 0) P.vcost[u] += (unsigned long long)(clock64() - t_vert);
+            if (!MULTI && P.vcost && lane == 0) P.vcost[u] += (unsigned long long)(clock64() - t_vert);
         }
     }
 
     // ---------------------------------------------------------------- totals
-    if (BATCH) {
+    if (MULTI) {
         if (cur_graph != 0xffffffffu) flush_graph(cnt, lane, gout);
     } else {
         pk_flush(cnt, lane);
@@ -596,7 +632,8 @@ __global__ void k_plan_emit(GraphDev g, uint32_t u_end, const uint32_t* pos, con
 }
 
 std::atomic<uint64_t> g_table_uploaded{0};
-std::atomic<uint64_t> g_attr_set[4] = {{0}, {0}, {0}, {0}};
+std::atomic<uint64_t> g_attr_set[6] = {{0}, {0}, {0}, {0}, {0}, {0}};
+std::atomic<int> g_dyn_limit[6] = {{0}, {0}, {0}, {0}, {0}, {0}};   // per kernel form: optin - static smem
 
 size_t census_smem(uint32_t algo, uint32_t chunk) {
     return sizeof(uint32_t) * (algo == TC_ALGO_UNION ? 3ull : 4ull) * chunk + sizeof(uint32_t) * (chunk / 16) +
@@ -619,14 +656,23 @@ tc_status prepare_device(cudaStream_t st, int algo, size_t smem) {
     TC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int limit = optin - 256;   // leave room for the kernel's static shared variables
     if ((int)smem > limit) return fail(TC_ERR_ARG, "chunk_entries too large for this GPU's shared memory");
-    const void* fns[4] = {(const void*)k_census<TC_ALGO_UNION, false>, (const void*)k_census<TC_ALGO_SUFFIX, false>,
-                          (const void*)k_census<TC_ALGO_UNION, true>, (const void*)k_census<TC_ALGO_SUFFIX, true>};
-    for (int b = 0; b < 2; ++b) {
+    const void* fns[6] = {(const void*)k_census<TC_ALGO_UNION, kModeSingle>, (const void*)k_census<TC_ALGO_SUFFIX, kModeSingle>,
+                          (const void*)k_census<TC_ALGO_UNION, kModeBatch>, (const void*)k_census<TC_ALGO_SUFFIX, kModeBatch>,
+                          (const void*)k_census<TC_ALGO_UNION, kModeWave>, (const void*)k_census<TC_ALGO_SUFFIX, kModeWave>};
+    for (int b = 0; b < 3; ++b) {
         const int idx = 2 * b + algo;
         if (!(g_attr_set[idx].load() & bit)) {
-            TC_CUDA(cudaFuncSetAttribute(fns[idx], cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+            // dynamic + static shared memory may not exceed the opt-in limit; the wave form
+            // keeps its request descriptors in static shared memory
+            cudaFuncAttributes fa;
+            TC_CUDA(cudaFuncGetAttributes(&fa, fns[idx]));
+            const int lim_f = optin - (int)fa.sharedSizeBytes;
+            TC_CUDA(cudaFuncSetAttribute(fns[idx], cudaFuncAttributeMaxDynamicSharedMemorySize, lim_f));
+            g_dyn_limit[idx].store(lim_f);
             g_attr_set[idx].fetch_or(bit);
         }
+        if ((int)smem > g_dyn_limit[idx].load())
+            return fail(TC_ERR_ARG, "chunk_entries too large for this GPU's shared memory");
     }
     return TC_OK;
 }
@@ -698,9 +744,29 @@ tc_status census_launch_batch(const GraphDev* d_graphs, const Item* items, uint3
     P.wblocks = wblocks;
     P.n_wblocks = n_wblocks;
     const unsigned grid = (unsigned)census_grid(o);
-    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, true><<<grid, kThreads, smem, st>>>(P);
-    else k_census<TC_ALGO_SUFFIX, true><<<grid, kThreads, smem, st>>>(P);
+    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, kModeBatch><<<grid, kThreads, smem, st>>>(P);
+    else k_census<TC_ALGO_SUFFIX, kModeBatch><<<grid, kThreads, smem, st>>>(P);
     TC_LAUNCH("k_census (batched)");
+    return TC_OK;
+}
+
+tc_status census_launch_wave(const WaveReq* d_reqs, uint32_t n_reqs, uint32_t total_items, uint32_t total_blocks,
+                             const Opts& o, unsigned grid, uint32_t* ctr, cudaStream_t st) {
+    if (n_reqs > kMaxWave) return fail(TC_ERR_RANGE, "wave larger than kMaxWave requests");
+    const size_t smem = census_smem(o.algo, o.chunk);
+    Params P;
+    std::memset(&P, 0, sizeof(P));
+    P.n_items = total_items;
+    P.chunk = o.chunk;
+    P.warp_max = o.warp_max_deg;
+    P.ctr = ctr;
+    P.out = nullptr;
+    P.n_wblocks = total_blocks;
+    P.reqs = d_reqs;
+    P.n_reqs = n_reqs;
+    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, kModeWave><<<grid, kThreads, smem, st>>>(P);
+    else k_census<TC_ALGO_SUFFIX, kModeWave><<<grid, kThreads, smem, st>>>(P);
+    TC_LAUNCH("k_census (wave)");
     return TC_OK;
 }
 
@@ -725,6 +791,8 @@ tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items
     P.graphs = nullptr;
     P.wblocks = nullptr;
     P.n_wblocks = 0;
+    P.reqs = nullptr;
+    P.n_reqs = 0;
     const unsigned grid = (unsigned)census_grid(o);
     if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION><<<grid, kThreads, smem, st>>>(P);
     else k_census<TC_ALGO_SUFFIX><<<grid, kThreads, smem, st>>>(P);
@@ -753,6 +821,10 @@ tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream
     P.graphs = nullptr;
     P.wblocks = nullptr;
     P.n_wblocks = 0;
+    P.reqs = nullptr;
+    P.n_reqs = 0;
+    P.reqs = nullptr;
+    P.n_reqs = 0;
     const unsigned grid = (unsigned)census_grid(o);
     if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION><<<grid, kThreads, smem, st>>>(P);
     else k_census<TC_ALGO_SUFFIX><<<grid, kThreads, smem, st>>>(P);

@@ -72,6 +72,19 @@ struct tc_graph {
 
 namespace tc {
 
+// One request's slice in a serving wave: its graph, a range of its plan's CTA items, a range
+// of its one-warp-per-vertex tier, the prefixes of items / warp-tier blocks of the slices
+// before it in the wave, and its output (16 uint64 the kernel adds to).
+struct WaveReq {
+    GraphDev g;
+    const Item* items;
+    unsigned long long* out;
+    uint32_t n_items, item_pre, warp_begin, warp_end, block_pre, pad;
+};
+// slices per wave launch; 32 descriptors (2.3 KB of static shared memory) keep three CTAs
+// per SM at the default chunk
+constexpr uint32_t kMaxWave = 32;
+
 tc_status build_from_arcs(GraphStore& g, uint64_t m, const uint32_t* d_src, const uint32_t* d_dst, cudaStream_t st);
 tc_status build_from_csr(GraphStore& g, const uint64_t* d_off, const uint32_t* d_adj, cudaStream_t st);
 
@@ -89,6 +102,11 @@ int census_grid(const Opts& o);
 // d_out[16 g ..] (caller-zeroed); ctr: 4 zeroed uint32.  census_prepare must have run.
 tc_status census_launch_batch(const GraphDev* d_graphs, const Item* items, uint32_t n_items, const uint4* wblocks,
                               uint32_t n_wblocks, const Opts& o, uint32_t* ctr, unsigned long long* d_out, cudaStream_t st);
+// Wave census (serving): n_reqs request slices (device descriptors) with total_items CTA
+// items and total_blocks warp-tier blocks; slice r's counts are added to d_reqs[r].out;
+// ctr: 4 zeroed uint32.  census_prepare must have run.
+tc_status census_launch_wave(const WaveReq* d_reqs, uint32_t n_reqs, uint32_t total_items, uint32_t total_blocks,
+                             const Opts& o, unsigned grid, uint32_t* ctr, cudaStream_t st);
 // Per-device set-up of the census kernels (table upload, shared-memory limit); synchronises st.
 tc_status census_prepare(cudaStream_t st, const Opts& o);
 // Launch the census kernel on explicit buffers (no allocation): the work items, the id range

@@ -86,8 +86,29 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.tc_graph_create_arcs(1 << 30 + 1, 0, None, None, 0, None, None, ctypes.byref(out)) == tc.TC_ERR_RANGE
 
 
-def test_struct_layouts_match_header(lib):
+def test_struct_layouts_match_header(lib, tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets (the header
+    compiled by the host C compiler)."""
     import paper_1209_6308_gb300 as tc
-    assert ctypes.sizeof(tc.tc_options) == 16 * 4
-    assert ctypes.sizeof(tc.tc_graph_info) == 8 + 8 * 8
-    assert ctypes.sizeof(tc.tc_u128) == 16
+    structs = [tc.tc_u128, tc.tc_options, tc.tc_graph_info, tc.tc_server_options, tc.tc_serve_result,
+               tc.tc_server_info]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tc.h"', 'int main(void) {']
+    for st in structs:
+        name = st.__name__
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "size")] == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)
