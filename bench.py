@@ -59,6 +59,14 @@ def workload():
     return graphgen.rmat(WORKLOAD["scale"], WORKLOAD["edge_factor"], WORKLOAD["recip"], WORKLOAD["seed"])
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg: str) -> None:
+    """Progress line on stderr (seconds since start), so a slow section shows where it is."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -292,16 +300,17 @@ def serve_arm(tc, gs, arcs, census_opts, rate, seconds, warmup, seed):
     w = 1.0 / np.asarray(arcs, dtype=np.float64)
     choice = rng.choice(len(gs), total, p=w / w.sum())
     results, done = [], threading.Event()
-    with tc.Server({"quantum_us": 1000, "lanes": 2}, census_opts) as srv:
+    with tc.Server({"quantum_us": 1000, "lanes": 3}, census_opts) as srv:
         ids = [srv.add(g) for g in gs]
 
         def collector():
-            while len(results) < total and not done.is_set():
+            while not done.is_set():
                 results.extend(srv.poll(4096, timeout_ms=50))
 
         th = threading.Thread(target=collector, daemon=True)
         th.start()
         rid_graph, submit_lag = {}, []
+        overloaded = False
         t0 = time.perf_counter()
         for k in range(total):
             due = t0 + arrivals[k]
@@ -311,13 +320,27 @@ def serve_arm(tc, gs, arcs, census_opts, rate, seconds, warmup, seed):
                     break
                 if due - now > 2e-3:
                     time.sleep(due - now - 1e-3)
+            # an open-loop client against an overloaded server only grows the queue: stop
+            if k - len(results) > 20000 or now - t0 > 3.0 * (warmup + seconds):
+                overloaded = True
+                break
             submit_lag.append(time.perf_counter() - due)
             rid_graph[srv.submit(ids[choice[k]])] = (k, int(choice[k]))
-        srv.drain(600000)
-        th.join(timeout=60)
-        done.set()
+        drained = True
+        try:
+            srv.drain(120000)
+        except tc.TcError:
+            drained = False
+        finally:
+            done.set()
+            th.join(timeout=60)
+        results.extend(srv.poll(65536))
         stats = srv.stats()
+        trace = srv.trace()
     meas = [r for r in results if arrivals[rid_graph[r.id][0]] >= warmup]
+    if not meas:
+        return {"requests": 0, "completed": len(results), "overloaded": overloaded, "drained": drained,
+                "waves": stats["waves"]}, results, rid_graph
     lat = np.array([(r.done_ns - r.submit_ns) * 1e-6 for r in meas])
     t_first = min(r.submit_ns for r in meas)
     t_last = max(r.done_ns for r in meas)
@@ -331,7 +354,11 @@ def serve_arm(tc, gs, arcs, census_opts, rate, seconds, warmup, seed):
             "waves": stats["waves"], "slices_per_wave": stats["slices"] / max(stats["waves"], 1),
             "mean_waves_per_request": float(np.mean([r.waves for r in results])),
             "submit_lag_p99_ms": float(np.percentile(submit_lag, 99)) * 1e3,
-            "errors": int(sum(1 for r in results if r.status != 0)), "completed": len(results)}, results, rid_graph
+            "errors": int(sum(1 for r in results if r.status != 0)), "completed": len(results),
+            "overloaded": overloaded, "drained": drained, "ns_per_unit": stats["ns_per_unit"],
+            "wave_gpu_ms": {"p50": float(np.percentile([t["gpu_ms"] for t in trace], 50)),
+                            "p99": float(np.percentile([t["gpu_ms"] for t in trace], 99)),
+                            "max": float(max(t["gpu_ms"] for t in trace))} if trace else None}, results, rid_graph
 
 
 def serving_comparison(tc, torch, sh, model, args):
@@ -340,12 +367,13 @@ def serving_comparison(tc, torch, sh, model, args):
     t0 = time.perf_counter()
     pool = serving_pool()
     gen_s = time.perf_counter() - t0
+    log(f"serving pool generated in {gen_s:.1f}s")
     gs = [tc.Graph.from_arcs(n, s, d, stream=sh, options=learned.PLAIN) for (_, (n, s, d)) in pool]
     arcs = [len(s) for (_, (_, s, _)) in pool]
     want = [g.census(stream=sh, options=learned.PLAIN) for g in gs]
     out = {"workload": SERVE_POOL + f"_poisson{int(args.serve_rate)}_seed5", "graphs": len(gs),
            "pool_arcs": int(sum(arcs)), "rate_per_s": args.serve_rate, "measured_s": args.serve_seconds,
-           "warmup_s": args.serve_warmup, "quantum_us": 1000, "lanes": 2, "pool_generation_s": gen_s,
+           "warmup_s": args.serve_warmup, "quantum_us": 1000, "lanes": 3, "pool_generation_s": gen_s,
            "selection": "graph i with probability proportional to 1/arcs_i"}
     try:
         arms = [("plain", learned.PLAIN)]
@@ -355,6 +383,7 @@ def serving_comparison(tc, torch, sh, model, args):
             arms.append(("learned", learned.LEARNED))
         exact = True
         for name, opts in arms:
+            log(f"serving arm {name}")
             m, res, rid_graph = serve_arm(tc, gs, arcs, opts, args.serve_rate, args.serve_seconds,
                                           args.serve_warmup, 5)
             exact &= all(r.census() == want[rid_graph[r.id][1]] for r in res)
@@ -378,8 +407,10 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     algo = tc.TC_ALGO_SUFFIX if args.algo == "suffix" else tc.TC_ALGO_UNION
     opts = {"algo": algo}
+    log("generating the workload")
     n, s, d = workload()
     arcs = len(s)
+    log(f"workload: n={n} arcs={arcs}")
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
 
@@ -397,6 +428,7 @@ def run_gpu(args):
             flush.zero_()
             one_census()
     torch.cuda.synchronize()
+    log("warm-up done; timing")
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if dist:
@@ -428,10 +460,14 @@ def run_gpu(args):
     model = None
     if not args.no_learned and rank == 0:
         from paper_1209_6308_gb300 import learned
+        log("training the cost model")
         model, minfo = learned.train_cost_model(scales=(18, 19, 20, 21, 22), steps=800, stream=sh)
+        log(f"cost model trained: {minfo}")
         learned_line = learned_comparison(tc, g, stream, model, minfo)
+        log("learned comparison done")
     e2e_ms = []
     e2e_counts = None
+    log("end-to-end steps")
     for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -450,7 +486,9 @@ def run_gpu(args):
         return 0
     serve_line = None
     if not args.no_serve:
+        log("serving")
         serve_line = serving_comparison(tc, torch, sh, model, args)
+        log("serving done")
     if model is not None:
         tc.tc_costmodel_destroy(model)
 
@@ -484,9 +522,12 @@ def run_gpu(args):
     if serve_line is not None:
         line["serving"] = serve_line
     if not args.no_batch:
+        log("batched comparison")
         line["batched"] = batched_comparison(tc, torch, sh, stream, args.autotune_trials)
     if not args.no_cpu_baseline:
+        log("cpu baseline")
         line["cpu_baseline"] = cpu_baseline(n, s, d, arcs, args.cpu_sample_stride or CPU_STRIDE)
+    log("done")
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

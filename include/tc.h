@@ -248,8 +248,11 @@ tc_status tc_graph_attach_costmodel(tc_graph* g, const tc_costmodel* c, void* st
  * paper's monitoring use runs the census repeatedly at fixed intervals, Sec. 3) with
  * continuous batching: an engine thread runs each request as slices of its work items
  * (Fig. 5 step 2 pairs), up to 32 slices of different requests per launch ("wave") of the
- * census kernel, each wave sized to a target device time.  New requests join the next wave;
- * shortest remaining work goes first, and requests older than starve_ms before all others.
+ * census kernel, each wave sized to a target device time (at least the time of its heaviest
+ * item).  New requests join the next wave; shortest remaining work goes first, and the oldest
+ * request, once older than starve_ms, gets up to half of each wave.  With two or more lanes,
+ * lane 0 runs the requests larger than half a quantum's work in waves that leave one CTA slot
+ * per SM free, and the other lanes (high-priority streams) run the small ones in that slot.
  * Counts are exactly those of tc_census.
  *
  * Thread safety: submit, poll, drain and stats may be called from any thread; add/remove
@@ -264,7 +267,7 @@ typedef struct {
     uint32_t max_active;      /* requests in execution at once, one output slot each (0 = 1024) */
     uint32_t max_pending;     /* queued requests beyond which submit returns TC_ERR_BUSY (0 = 65536) */
     uint32_t quantum_us;      /* target device time of one wave (0 = 1000) */
-    uint32_t lanes;           /* CUDA streams waves are issued on, 1..4 (0 = 2) */
+    uint32_t lanes;           /* CUDA streams waves are issued on, 1..4 (0 = 3): one bulk lane, the rest express */
     uint32_t starve_ms;       /* age after which a request is served before all younger ones (0 = 50) */
     uint32_t reserved[9];
 } tc_server_options;
@@ -314,6 +317,17 @@ tc_status tc_server_poll(tc_server* s, tc_serve_result* out, uint32_t max, uint3
  * not); returns the first engine error if one occurred.  Results stay queued for poll. */
 tc_status tc_server_drain(tc_server* s, uint32_t timeout_ms);
 tc_status tc_server_stats(tc_server* s, tc_server_info* info);
+/* One wave of the engine, for tracing: launch and completion time (tc_server_now_ns clock),
+ * device time (CUDA events), the slice cost model's units in it and the budget it was sized
+ * to, and its counts of slices, finished requests, CTA items and 32-vertex warp-tier blocks. */
+typedef struct {
+    uint64_t launch_ns, done_ns;
+    uint64_t units, budget;
+    float gpu_ms;
+    uint32_t lane, slices, finished, items, blocks;
+} tc_wave_record;
+/* The last min(max, 8192) waves, oldest first; *count = number written. */
+tc_status tc_server_trace(tc_server* s, tc_wave_record* out, uint32_t max, uint32_t* count);
 /* Total cost units (element units) of a registered graph's census and its work counts. */
 tc_status tc_server_graph_units(tc_server* s, uint32_t graph_id, uint64_t* units, uint32_t* n_items,
                                 uint32_t* n_blocks);

@@ -82,6 +82,16 @@ class tc_server_info(ctypes.Structure):
                 for k, _ in self._fields_ if k != "reserved"}
 
 
+class tc_wave_record(ctypes.Structure):
+    _fields_ = [("launch_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64), ("units", ctypes.c_uint64),
+                ("budget", ctypes.c_uint64), ("gpu_ms", ctypes.c_float), ("lane", ctypes.c_uint32),
+                ("slices", ctypes.c_uint32), ("finished", ctypes.c_uint32), ("items", ctypes.c_uint32),
+                ("blocks", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: (float(getattr(self, k)) if k == "gpu_ms" else int(getattr(self, k))) for k, _ in self._fields_}
+
+
 _lib = None
 _VP, _U32, _U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
 
@@ -137,6 +147,7 @@ SIGNATURES = {
     "tc_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(tc_server_info)]),
     "tc_server_graph_units": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(_U64), ctypes.POINTER(_U32),
                                              ctypes.POINTER(_U32)]),
+    "tc_server_trace": (ctypes.c_int, [_VP, ctypes.POINTER(tc_wave_record), _U32, ctypes.POINTER(_U32)]),
     "tc_server_destroy": (None, [_VP]),
     "tc_tricode_table": (None, [ctypes.POINTER(ctypes.c_uint8)]),
 }
@@ -542,6 +553,14 @@ def tc_server_graph_units(s: int, graph_id: int):
     return int(u.value), int(ni.value), int(nb.value)
 
 
+def tc_server_trace(s: int, max_records: int = 8192) -> list:
+    """The last waves of the engine (oldest first) as dicts."""
+    buf = (tc_wave_record * max(max_records, 1))()
+    cnt = _U32()
+    _check(load().tc_server_trace(s, buf, max_records, ctypes.byref(cnt)), "tc_server_trace")
+    return [buf[i].as_dict() for i in range(cnt.value)]
+
+
 def tc_server_destroy(s: int) -> None:
     if s:
         load().tc_server_destroy(s)
@@ -570,6 +589,9 @@ class Server:
 
     def stats(self) -> dict:
         return tc_server_stats(self.handle)
+
+    def trace(self, max_records: int = 8192) -> list:
+        return tc_server_trace(self.handle, max_records)
 
     def close(self):
         tc_server_destroy(self.handle)

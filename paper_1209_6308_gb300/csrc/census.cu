@@ -54,6 +54,7 @@ struct Params {
     const Item* items;
     uint32_t n_items;
     uint32_t warp_begin, warp_end;
+    uint32_t wshift;               // warp tier: a warp takes 2^wshift consecutive vertices per grab
     uint32_t chunk;
     uint32_t warp_max;
     uint32_t* ctr;                 // [0] next item, [1] next warp-tier vertex block
@@ -481,8 +482,8 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
             if (b >= P.n_wblocks) break;
             const uint32_t r = wave_find(P.n_reqs, b, [&](uint32_t q) { return sReq[q].block_pre; });
             if (r != cur_graph) use_graph(r);
-            u0 = sReq[r].warp_begin + 32u * (b - sReq[r].block_pre);
-            u1 = min(u0 + 32u, sReq[r].warp_end);
+            u0 = sReq[r].warp_begin + ((b - sReq[r].block_pre) << sReq[r].pad);
+            u1 = min(u0 + (1u << sReq[r].pad), sReq[r].warp_end);
         } else if (MODE == kModeBatch) {
             uint32_t b = 0;
             if (lane == 0) b = atomicAdd(&P.ctr[1], 1u);
@@ -494,11 +495,11 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
             u1 = wb.y;
         } else {
             uint32_t ub = 0;
-            if (lane == 0) ub = atomicAdd(&P.ctr[1], 32u);
+            if (lane == 0) ub = atomicAdd(&P.ctr[1], 1u << P.wshift);
             ub = __shfl_sync(0xffffffffu, ub, 0);
             if (ub >= P.warp_end - P.warp_begin) break;
             u0 = P.warp_begin + ub;
-            u1 = min(u0 + 32u, P.warp_end);
+            u1 = min(u0 + (1u << P.wshift), P.warp_end);
         }
         for (uint32_t u = u0; u < u1; ++u) {
             const uint64_t ubase = off[u];
@@ -729,6 +730,15 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out) {
 
 int census_grid(const Opts& o) { return sm_count() * (int)o.ctas_per_sm; }
 
+uint32_t warp_block_shift(uint64_t vertices, unsigned grid) {
+    // the largest grab of at most 32 vertices that still leaves every warp about four grabs:
+    // with fewer, one warp walking 32 vertices' pairs in series sets the kernel's duration
+    const uint64_t target = vertices / (4ull * grid * kWarps);
+    uint32_t s = 5;
+    while (s > 0 && (1ull << s) > target) --s;
+    return s;
+}
+
 tc_status census_launch_batch(const GraphDev* d_graphs, const Item* items, uint32_t n_items, const uint4* wblocks,
                               uint32_t n_wblocks, const Opts& o, uint32_t* ctr, unsigned long long* d_out, cudaStream_t st) {
     const size_t smem = census_smem(o.algo, o.chunk);
@@ -782,6 +792,7 @@ tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items
     P.n_items = n_items;
     P.warp_begin = warp_begin;
     P.warp_end = warp_end;
+    P.wshift = warp_block_shift(warp_end - warp_begin, (unsigned)census_grid(o));
     P.chunk = o.chunk;
     P.warp_max = o.warp_max_deg;
     P.ctr = ctr;
@@ -812,6 +823,7 @@ tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream
     P.n_items = p.n_items;
     P.warp_begin = p.warp_begin;
     P.warp_end = p.warp_end;
+    P.wshift = warp_block_shift(p.warp_end - p.warp_begin, (unsigned)census_grid(o));
     P.chunk = o.chunk;
     P.warp_max = o.warp_max_deg;
     P.ctr = g.ctr.as<uint32_t>();

@@ -73,8 +73,9 @@ struct tc_graph {
 namespace tc {
 
 // One request's slice in a serving wave: its graph, a range of its plan's CTA items, a range
-// of its one-warp-per-vertex tier, the prefixes of items / warp-tier blocks of the slices
-// before it in the wave, and its output (16 uint64 the kernel adds to).
+// of its one-warp-per-vertex tier (taken 2^pad vertices per warp-tier block), the prefixes of
+// items / warp-tier blocks of the slices before it in the wave, and its output (16 uint64 the
+// kernel adds to).
 struct WaveReq {
     GraphDev g;
     const Item* items;
@@ -97,6 +98,9 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out);
 tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16,
                          unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr);
 int census_grid(const Opts& o);
+// log2 of the vertices a warp takes per grab in the one-warp-per-vertex tier, for `vertices`
+// such vertices and a grid of `grid` CTAs (0..5).
+uint32_t warp_block_shift(uint64_t vertices, unsigned grid);
 // Batched census: one launch over several graphs (d_graphs on the device); item.pad is the
 // graph index, wblocks are (u0, u1, graph, 0) warp-tier blocks; graph g's counts are added to
 // d_out[16 g ..] (caller-zeroed); ctr: 4 zeroed uint32.  census_prepare must have run.

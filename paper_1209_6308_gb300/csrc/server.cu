@@ -11,11 +11,15 @@
 // one to finish, and the device always has a full wave queued.  Slices are chosen shortest
 // remaining work first, with requests older than starve_ms served first.
 //
-// Each request is pinned to one of `lanes` streams at its first slice; every slice of it runs
-// on that stream, so its 16 counters (one slot of a device array, added to by each slice) are
-// complete, in stream order, when the wave holding its last slice has run.  That wave ends
-// with a small kernel that copies the finished slots to mapped host memory and zeroes them for
-// reuse.  Waves on different lanes overlap on the device (one's tail with the next's head).
+// Lanes: each request is pinned to one CUDA stream ("lane") at its first slice, and every
+// slice of it runs there, so its 16 counters (one slot of a device array, added to by each
+// slice) are complete, in stream order, when the wave holding its last slice has run.  That
+// wave ends with a small kernel that copies the finished slots to mapped host memory and
+// zeroes them for reuse.  With two or more lanes, lane 0 is the bulk lane: requests larger
+// than half of the quantum's work run there, in waves of one CTA fewer per SM than the census
+// grid; the other lanes are express lanes on high-priority streams for the small requests,
+// which thus start in the CTA slot the bulk waves leave free instead of waiting for a long
+// bulk wave (whose duration is bounded below by its longest hub item) to end.
 //
 // Memory admission: tc_server_add_graph admits a graph only while the resident bytes (CSR,
 // relabelling, the server's copy of the work plan) stay within the budget; refused graphs get
@@ -46,8 +50,9 @@ uint64_t steady_ns() {
 constexpr uint64_t kPairUnits = 16;   // per-pair overhead in element units (offsets, the pair fold)
 
 // Cost of CTA item i in element units: staging N[u] once, then N[v] plus a fixed overhead per
-// pair (and the union walk's u side, which visits about half of N[u] per pair).  One warp per item.
-__global__ void k_item_cost(GraphDev g, const Item* __restrict__ items, uint32_t n_items, int algo,
+// pair and per pair and chunk of N[u] (the pair's cursor), and the union walk's u side, which
+// visits about half of N[u] per pair.  One warp per item.
+__global__ void k_item_cost(GraphDev g, const Item* __restrict__ items, uint32_t n_items, int algo, uint32_t chunk,
                             unsigned long long* cost) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -62,7 +67,8 @@ __global__ void k_item_cost(GraphDev g, const Item* __restrict__ items, uint32_t
         }
         c = __reduce_add_sync(0xffffffffu, (unsigned)(c & 0xffffffffu)) +
             ((unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)(c >> 32)) << 32);
-        if (lane == 0) cost[i] = c + du;
+        const uint64_t chunks = (du + chunk - 1) / chunk;
+        if (lane == 0) cost[i] = c + du + (uint64_t)(it.j1 - it.j0) * chunks * kPairUnits;
     }
 }
 
@@ -142,9 +148,12 @@ struct Wave {
     unsigned long long* h_res = nullptr; // mapped pinned [kMaxWave][16]
     unsigned long long* d_res = nullptr; // its device address
     std::vector<Req*> slices, finishing;
-    uint64_t units = 0;
+    uint64_t units = 0, budget = 0, launch_ns = 0;
+    uint32_t items = 0, blocks = 0, work = 0;
     bool used = false;
 };
+
+constexpr uint32_t kTrace = 8192;        // wave records kept for tc_server_trace
 
 constexpr size_t kDescBytes = sizeof(WaveReq) * kMaxWave + 16;
 constexpr int kDepth = 2;                // waves in flight per lane
@@ -165,7 +174,8 @@ struct tc_server {
     uint32_t max_active = 1024, max_pending = 65536, lanes_n = 2;
     uint64_t quantum_ns = 1000000, starve_ns = 50000000;
     int device = 0;
-    unsigned grid = 0;
+    unsigned grid = 0;          // census grid (every CTA slot)
+    unsigned grid_bulk = 0;     // bulk-lane waves when express lanes exist
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -181,6 +191,8 @@ struct tc_server {
     double ns_per_unit = 0.004;
     tc_status err = TC_OK;
     std::string err_msg;
+    std::vector<tc_wave_record> trace;   // ring of the last kTrace waves (under mu)
+    uint64_t trace_next = 0;
 
     // engine-owned
     std::vector<std::unique_ptr<tc::Req>> active;
@@ -257,13 +269,32 @@ bool retire(tc_server* s) {
                 if (cudaEventElapsedTime(&ms, w->e0, w->e1) == cudaSuccess) {
                     std::lock_guard<std::mutex> lk(s->mu);
                     s->gpu_ms += ms;
-                    // calibrate element units -> device time on waves big enough to dominate
-                    // the launch overhead
+                    // calibrate element units -> device time only on waves that fill the GPU
+                    // (a wave's time is bounded below by its longest item, so sparse waves
+                    // would overstate the cost per unit), with each step limited to 2x
                     const double budget = (double)s->quantum_ns / s->ns_per_unit;
-                    if ((double)w->units > 0.25 * budget) {
-                        const double r = (double)ms * 1e6 / (double)w->units;
+                    const bool calib = s->lanes_n < 2 || L == 0;
+                    if (calib && w->work >= (s->lanes_n < 2 ? s->grid : s->grid_bulk) &&
+                        (double)w->units > 0.25 * budget) {
+                        const double r = std::min(2.0 * s->ns_per_unit,
+                                                  std::max(0.5 * s->ns_per_unit, (double)ms * 1e6 / (double)w->units));
                         s->ns_per_unit = 0.75 * s->ns_per_unit + 0.25 * r;
                     }
+                    tc_wave_record rec;
+                    std::memset(&rec, 0, sizeof(rec));
+                    rec.launch_ns = w->launch_ns;
+                    rec.done_ns = t_done;
+                    rec.units = w->units;
+                    rec.budget = w->budget;
+                    rec.gpu_ms = ms;
+                    rec.lane = L;
+                    rec.slices = (uint32_t)w->slices.size();
+                    rec.finished = (uint32_t)w->finishing.size();
+                    rec.items = w->items;
+                    rec.blocks = w->blocks;
+                    if (s->trace.size() < kTrace) s->trace.push_back(rec);
+                    else s->trace[s->trace_next % kTrace] = rec;
+                    s->trace_next++;
                 }
             }
             for (Req* r : w->slices) r->inflight--;
@@ -333,9 +364,23 @@ void admit(tc_server* s) {
     s->cv_done.notify_all();
 }
 
-bool has_work(const tc_server* s, int L) {
+// Whether lane L may take request r: its own lane, or, for a request not yet started, the
+// bulk lane (0) for large requests and an express lane for small ones (one lane takes all).
+bool eligible(const tc_server* s, const Req* r, int L, uint64_t express_units) {
+    if (r->left == 0 || r->status != TC_OK) return false;
+    if (r->lane >= 0) return r->lane == L;
+    if (s->lanes_n < 2) return true;
+    return (L == 0) == (r->left > express_units);
+}
+
+uint64_t express_units(tc_server* s) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    return (uint64_t)((double)s->quantum_ns / s->ns_per_unit / 2.0);
+}
+
+bool has_work(const tc_server* s, int L, uint64_t xu) {
     for (const auto& r : s->active)
-        if ((r->lane == L || r->lane < 0) && r->left > 0 && r->status == TC_OK) return true;
+        if (eligible(s, r.get(), L, xu)) return true;
     return false;
 }
 
@@ -347,38 +392,56 @@ void launch_wave(tc_server* s, int L) {
         if (!x.used) { w = &x; break; }
     if (!w) return;
     const uint64_t now = steady_ns();
+    const uint64_t xu = express_units(s);
+    const bool split = s->lanes_n >= 2, bulk = !split || L == 0;
+    const unsigned lane_grid = split && L == 0 ? s->grid_bulk : s->grid;
     std::vector<Req*> cand;
     for (auto& r : s->active)
-        if ((r->lane == L || r->lane < 0) && r->left > 0 && r->status == TC_OK) cand.push_back(r.get());
-    std::sort(cand.begin(), cand.end(), [&](const Req* a, const Req* b) {
-        const bool sa = now - a->t_submit > s->starve_ns, sb = now - b->t_submit > s->starve_ns;
-        if (sa != sb) return sa;
-        if (sa) return a->t_submit < b->t_submit;
+        if (eligible(s, r.get(), L, xu)) cand.push_back(r.get());
+    // shortest remaining work first; the oldest request, once older than starve_ns, goes
+    // first with at most half of the wave's budget, so it progresses without holding the lane
+    std::sort(cand.begin(), cand.end(), [](const Req* a, const Req* b) {
         if (a->left != b->left) return a->left < b->left;
         return a->id < b->id;
     });
+    Req* starved = nullptr;
+    for (Req* r : cand)
+        if (now - r->t_submit > s->starve_ns && (!starved || r->t_submit < starved->t_submit)) starved = r;
+    if (starved) {
+        cand.erase(std::find(cand.begin(), cand.end(), starved));
+        cand.insert(cand.begin(), starved);
+    }
     double nspu;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         nspu = s->ns_per_unit;
     }
-    uint64_t budget = (uint64_t)std::max(1.0, (double)s->quantum_ns / nspu);
-    uint32_t n = 0, tot_items = 0, tot_blocks = 0;
-    uint64_t units = 0;
+    const uint64_t budget0 = (uint64_t)std::max(1.0, (double)s->quantum_ns / nspu);
+    // A wave lasts at least as long as its heaviest item (one CTA runs it), so once a wave
+    // holds an item of h units it may hold h x grid units at no cost in time: the effective
+    // budget is max(quantum budget, h x grid), and heavy-item requests fill the GPU by
+    // themselves while the rest of that time goes to other requests.  Items are in plan order
+    // (heaviest vertices first), so a slice's first item is its heaviest.
+    uint64_t heavy = 0, units = 0;
+    auto eff_budget = [&]() { return std::max<uint64_t>(budget0, heavy * lane_grid); };
+    uint32_t n = 0, tot_items = 0, tot_blocks = 0, work = 0;
     const size_t zero_ctr_off = sizeof(WaveReq) * kMaxWave;
     for (Req* r : cand) {
         if (n == kMaxWave) break;
-        if (n > 0 && budget == 0) break;
+        if (n > 0 && units >= eff_budget()) break;
         SGraph& G = *r->G;
         const uint32_t i0 = r->ic, b0 = r->bc;
         uint32_t i1 = i0, b1 = b0;
         uint64_t took = 0;
+        if (i0 < G.n_items && bulk) heavy = std::max<uint64_t>(heavy, G.item_pre[i0 + 1] - G.item_pre[i0]);
+        const uint64_t left_b = eff_budget() > units ? eff_budget() - units : 0;
+        const uint64_t cap = (r == starved && cand.size() > 1) ? std::max<uint64_t>(left_b / 2, 1) : left_b;
         if (i0 < G.n_items) {
-            i1 = slice_end(G.item_pre, i0, G.n_items, budget, n == 0);
+            i1 = slice_end(G.item_pre, i0, G.n_items, cap, n == 0);
             took = G.item_pre[i1] - G.item_pre[i0];
         }
         if (i1 == G.n_items && b0 < G.n_blocks) {
-            b1 = slice_end(G.block_pre, b0, G.n_blocks, took < budget ? budget - took : 0, n == 0 && i1 == i0);
+            b1 = slice_end(G.block_pre, b0, G.n_blocks, took < cap ? cap - took : 0, n == 0 && i1 == i0);
             took += G.block_pre[b1] - G.block_pre[b0];
         }
         if (i1 == i0 && b1 == b0) continue;   // its next unit does not fit; try the others
@@ -391,11 +454,11 @@ void launch_wave(tc_server* s, int L) {
         d.warp_begin = G.warp_begin + 32u * b0;
         d.warp_end = std::min(G.warp_begin + 32u * b1, G.warp_end);
         if (b1 == b0) d.warp_end = d.warp_begin;
-        d.block_pre = tot_blocks;
+        d.block_pre = 0;
         d.pad = 0;
         tot_items += i1 - i0;
         tot_blocks += b1 - b0;
-        budget = took >= budget ? 0 : budget - took;
+        work += (i1 - i0) + 4 * (b1 - b0);
         units += took;
         r->ic = i1;
         r->bc = b1;
@@ -412,11 +475,28 @@ void launch_wave(tc_server* s, int L) {
         ++n;
     }
     if (n == 0) return;
+    // warp-tier blocks: the cost model slices in 32-vertex blocks; the kernel takes smaller
+    // ones when the wave has few warp-tier vertices, so no warp walks 32 vertices alone
+    uint64_t wverts = 0;
+    for (uint32_t k = 0; k < n; ++k) wverts += w->h_desc[k].warp_end - w->h_desc[k].warp_begin;
+    const uint32_t ws = warp_block_shift(wverts, lane_grid);
+    tot_blocks = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        WaveReq& d = w->h_desc[k];
+        d.pad = ws;
+        d.block_pre = tot_blocks;
+        tot_blocks += (d.warp_end - d.warp_begin + (1u << ws) - 1) >> ws;
+    }
     std::memset(reinterpret_cast<unsigned char*>(w->h_desc) + zero_ctr_off, 0, 16);
     w->units = units;
+    w->budget = eff_budget();
+    w->items = tot_items;
+    w->blocks = tot_blocks;
+    w->work = work;
+    w->launch_ns = now;
     w->used = true;
     cudaStream_t st = ln.st;
-    unsigned grid = std::min<unsigned>(s->grid, std::max<unsigned>(1u, tot_items + (tot_blocks + 7) / 8));
+    unsigned grid = std::min<unsigned>(lane_grid, std::max<unsigned>(1u, tot_items + (tot_blocks + 7) / 8));
     cudaError_t e = cudaMemcpyAsync(w->d_desc, w->h_desc, kDescBytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(w->e0, st);
     tc_status ks = TC_OK;
@@ -478,9 +558,10 @@ void engine_main(tc_server* s) {
         for (uint32_t L = 0; L < s->lanes_n; ++L) order[L] = (int)L;
         std::sort(order, order + s->lanes_n,
                   [&](int a, int b) { return s->lanes[a].inflight.size() < s->lanes[b].inflight.size(); });
+        const uint64_t xu = express_units(s);
         for (uint32_t k = 0; k < s->lanes_n; ++k) {
             const int L = order[k];
-            if (s->lanes[L].inflight.size() < (size_t)kDepth && has_work(s, L)) {
+            if (s->lanes[L].inflight.size() < (size_t)kDepth && has_work(s, L, xu)) {
                 const uint64_t before = s->n_waves;
                 launch_wave(s, L);
                 did |= s->n_waves != before;
@@ -532,7 +613,7 @@ tc_status tc_server_create(const tc_server_options* opt, tc_server** out) {
         return fail(TC_ERR_ARG, "unknown schedule");
     s->max_active = o.max_active ? o.max_active : 1024;
     s->max_pending = o.max_pending ? o.max_pending : 65536;
-    s->lanes_n = o.lanes ? o.lanes : 2;
+    s->lanes_n = o.lanes ? o.lanes : 3;
     s->quantum_ns = (uint64_t)(o.quantum_us ? o.quantum_us : 1000) * 1000ull;
     s->starve_ns = (uint64_t)(o.starve_ms ? o.starve_ms : 50) * 1000000ull;
     TC_CUDA(cudaGetDevice(&s->device));
@@ -540,13 +621,17 @@ tc_status tc_server_create(const tc_server_options* opt, tc_server** out) {
     TC_CUDA(cudaMemGetInfo(&fr, &total));
     s->budget = o.budget_bytes ? o.budget_bytes : (uint64_t)(0.9 * (double)total);
     s->grid = (unsigned)census_grid(s->opts);
+    const unsigned sms = (unsigned)sm_count();
+    s->grid_bulk = s->opts.ctas_per_sm > 1 ? sms * (s->opts.ctas_per_sm - 1) : sms;
+    int prio_lo = 0, prio_hi = 0;
+    TC_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
     TC_TRY(s->slots.alloc_persistent(sizeof(unsigned long long) * 16ull * s->max_active));
     TC_CUDA(cudaMemset(s->slots.p, 0, s->slots.bytes));
     for (uint32_t i = 0; i < s->max_active; ++i) s->free_slots.push_back(s->max_active - 1 - i);
     bool ok = true;
     for (uint32_t L = 0; L < s->lanes_n && ok; ++L) {
         Lane& ln = s->lanes[L];
-        ok = cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking) == cudaSuccess;
+        ok = cudaStreamCreateWithPriority(&ln.st, cudaStreamNonBlocking, L == 0 ? prio_lo : prio_hi) == cudaSuccess;
         for (auto& w : ln.waves) {
             if (!ok) break;
             ok = cudaEventCreate(&w.e0) == cudaSuccess && cudaEventCreate(&w.e1) == cudaSuccess &&
@@ -619,7 +704,7 @@ tc_status tc_server_add_graph(tc_server* s, tc_graph* g, void* stream, uint32_t*
         return unreserve(TC_ERR_OOM);
     if (G->n_items)
         k_item_cost<<<grid_for((uint64_t)G->n_items * 32, 256, 8192), 256, 0, st>>>(
-            G->gd, G->items.as<Item>(), G->n_items, (int)s->opts.algo, ci.as<unsigned long long>());
+            G->gd, G->items.as<Item>(), G->n_items, (int)s->opts.algo, s->opts.chunk, ci.as<unsigned long long>());
     if (G->n_blocks)
         k_block_cost<<<grid_for((uint64_t)G->n_blocks * 32, 256, 8192), 256, 0, st>>>(
             G->gd, G->warp_begin, G->warp_end, G->n_blocks, (int)s->opts.algo, cb.as<unsigned long long>());
@@ -733,6 +818,19 @@ tc_status tc_server_graph_units(tc_server* s, uint32_t graph_id, uint64_t* units
     if (units) *units = it->second->units();
     if (n_items) *n_items = it->second->n_items;
     if (n_blocks) *n_blocks = it->second->n_blocks;
+    return TC_OK;
+}
+
+tc_status tc_server_trace(tc_server* s, tc_wave_record* out, uint32_t max, uint32_t* count) {
+    if (!s || !count || (max && !out)) return fail(TC_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const uint64_t have = std::min<uint64_t>(s->trace.size(), max);
+    // oldest first among the last `have` records
+    for (uint64_t k = 0; k < have; ++k) {
+        const uint64_t idx = s->trace_next - have + k;
+        out[k] = s->trace[idx % kTrace];
+    }
+    *count = (uint32_t)have;
     return TC_OK;
 }
 

@@ -91,7 +91,7 @@ def test_struct_layouts_match_header(lib, tmp_path):
     compiled by the host C compiler)."""
     import paper_1209_6308_gb300 as tc
     structs = [tc.tc_u128, tc.tc_options, tc.tc_graph_info, tc.tc_server_options, tc.tc_serve_result,
-               tc.tc_server_info]
+               tc.tc_server_info, tc.tc_wave_record]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tc.h"', 'int main(void) {']
     for st in structs:
         name = st.__name__
