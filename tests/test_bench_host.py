@@ -1,0 +1,72 @@
+"""Host logic of bench.py that needs no GPU: the multi-rank reduction (world_size 2 over gloo
+on the CPU, the same calls the NCCL ranks make), the whole-job value, the command-line
+defaults, and the reference arm's behaviour on ranks other than 0."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, times, out):
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        dist.barrier()
+        ms = bench.max_over_ranks(dist, times[rank], "cpu")
+        out.put((rank, ms, bench.job_value(world, 1000, ms)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_job_value_with_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    times = [12.5, 40.0]
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, times, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, value in res:
+        assert ms == 40.0                      # every rank sees the slowest rank's time
+        assert value == pytest.approx(2 * 1000 / 0.040)
+
+
+def test_single_process_reduction_is_the_identity():
+    import bench
+    assert bench.max_over_ranks(None, 3.25, "cpu") == 3.25
+    assert bench.job_value(1, 500, 2.0) == pytest.approx(250000.0)
+
+
+def test_defaults_finish_in_minutes(monkeypatch):
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert a.gpus == 1 and a.warmup >= 3 and 1 <= a.steps <= 20
+    assert a.impl == "ours" and a.serve_seconds <= 30
+
+
+def test_reference_arm_on_other_ranks_exits_without_work(monkeypatch):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
+    called = []
+    monkeypatch.setattr(bench, "workload", lambda: called.append(1))
+    assert bench.run_reference(bench.parse()) == 0
+    assert not called

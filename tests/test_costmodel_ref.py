@@ -43,3 +43,48 @@ def test_finite_differences_catch_a_wrong_sign():
     fd = (ref.loss(pp, X, T, m, s, tm) - ref.loss(pm, X, T, m, s, tm)) / (2 * h)
     assert abs(fd - g[i]) < 1e-6 + 1e-5 * abs(fd)
     assert abs(fd - g_bad[i]) > 1e-4 * abs(fd) or abs(fd) < 1e-9
+
+
+def _one_path(a, b, c, d, wi=0, hi=0, hj=0):
+    """Parameters with a single path: feature wi -> hidden1 hi -> hidden2 hj -> output."""
+    p = np.zeros(ref.NUM_PARAMS)
+    p[hi * 4 + wi] = a                                 # W1[hi][wi]
+    p[4 * 32 + 32 + hj * 32 + hi] = b                  # W2[hj][hi]
+    p[4 * 32 + 32 + 32 * 32 + 32 + hj] = c             # W3[hj]
+    p[-1] = d                                          # b3
+    return p
+
+
+def test_forward_of_the_zero_network_is_its_output_bias():
+    p = np.zeros(ref.NUM_PARAMS)
+    p[-1] = 0.75
+    X = np.random.default_rng(4).normal(size=(10, 4))
+    y, _ = ref.forward(p, X, np.zeros(4), np.ones(4), 3.0)
+    assert np.allclose(y, 0.75)
+
+
+def test_forward_of_a_single_path_by_hand():
+    # y = c tanh(b tanh(a (x_2 - m_2) / s_2)) + d, the composition the network's definition
+    # gives for one feature -> one hidden unit -> one hidden unit -> output
+    a, b, c, d = 0.7, -1.3, 2.0, 0.25
+    p = _one_path(a, b, c, d, wi=2, hi=5, hj=9)
+    X = np.array([[0.0, 0.0, 1.0, 0.0], [9.0, 9.0, -2.0, 9.0], [1.0, 2.0, 4.0, 3.0]])
+    mean, std = np.array([0.0, 0.0, 1.0, 0.0]), np.array([1.0, 1.0, 2.0, 1.0])
+    y, _ = ref.forward(p, X, mean, std, 0.0)
+    for k, x2 in enumerate([1.0, -2.0, 4.0]):
+        z = (x2 - 1.0) / 2.0
+        want = c * np.tanh(b * np.tanh(a * z)) + d
+        assert abs(y[k] - want) < 1e-12
+    # the loss is the mean squared error against the centred target
+    T = np.array([5.0, 6.0, 7.0])
+    assert abs(ref.loss(p, X, T, mean, std, 4.0) - np.mean((y - (T - 4.0)) ** 2)) < 1e-12
+
+
+def test_forward_ignores_unconnected_features():
+    p = _one_path(1.1, 0.9, -0.5, 0.0, wi=1)
+    X = np.random.default_rng(5).normal(size=(6, 4))
+    X2 = X.copy()
+    X2[:, [0, 2, 3]] += 10.0
+    y1, _ = ref.forward(p, X, np.zeros(4), np.ones(4), 0.0)
+    y2, _ = ref.forward(p, X2, np.zeros(4), np.ones(4), 0.0)
+    assert np.allclose(y1, y2)
