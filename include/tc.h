@@ -85,8 +85,13 @@ typedef struct {
     uint64_t dups_dropped;    /* repeated arcs in the input */
     uint64_t sum_d2;          /* sum over vertices of deg^2 = merge steps of the full union walk */
     uint64_t sum_dv_upper;    /* sum over upper pairs u<v of deg(v) */
-    uint64_t bytes_alg;       /* algorithmic bytes of one census: 8(n+1) + 8 e_sym + sum(4 deg(v) + 16) + 128 */
+    uint64_t bytes_alg;       /* algorithmic bytes of one census (below) */
+    uint64_t sum_walk;        /* sum over upper pairs u<v of |{w in N(v): w > u}|: the N[v] entries
+                                 a census walks */
 } tc_graph_info;
+/* bytes_alg = 16(n+1) + 36 e_sym + 4 sum_walk + 128: the CSR read once (offsets 8(n+1), lists
+ * 8 e_sym), the per-pair tables (8(n+1) + 12 e_sym), 16 B of bookkeeping per pair, 4 B per
+ * N[v] entry walked, and the 16 counters. */
 
 /* Build a graph from an arc list (Sec. 6, Fig. 7).  src[i] -> dst[i] for i < m; self-loops
  * and repeated arcs are dropped and counted.  Ids >= n give TC_ERR_RANGE.  src/dst are

@@ -258,7 +258,8 @@ tc_status tc_graph_stats(const tc_graph* g, tc_graph_info* info) {
     info->dups_dropped = s.dups;
     info->sum_d2 = s.sum_d2;
     info->sum_dv_upper = s.sum_dv_upper;
-    info->bytes_alg = 8ull * (s.n + 1ull) + 8ull * s.e_sym + 4ull * s.sum_dv_upper + 16ull * s.e_sym + 128ull;
+    info->sum_walk = s.sum_walk;
+    info->bytes_alg = 16ull * (s.n + 1ull) + 36ull * s.e_sym + 4ull * s.sum_walk + 128ull;
     return TC_OK;
 }
 

@@ -153,6 +153,56 @@ __global__ void k_graph_sums(const uint64_t* off, const uint32_t* adj, const uin
     }
 }
 
+// Per upper pair tables.  One warp per vertex v takes N[v] in 32-entry blocks from the end,
+// keeping running counts of the direction classes of the entries behind the block and adding,
+// per lane, the block's entries after its own by ballot: so the lane at a lower neighbour
+// u = N[v][k] (k < up[v]) knows the counts of the entries after k, i.e. of the third vertices
+// w > u reached from v.  It finds the upper pair (u, v) in N[u] by binary search and writes
+// rp = k and vs = (class-1, class-2 counts).  wk[0] += the suffix lengths (the N[v] entries a
+// census walks).
+__global__ void k_pair_tables(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
+                              const uint32_t* __restrict__ up, const uint64_t* __restrict__ ub, uint32_t n,
+                              uint32_t* rp, uint2* vs, unsigned long long* wk) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t after = lane == 31 ? 0u : ~((2u << lane) - 1u);   // lanes above this one
+    unsigned long long walk = 0;
+    for (uint64_t v = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        const uint64_t ob = off[v];
+        const uint32_t dv = (uint32_t)(off[v + 1] - ob), lv = up[v];
+        uint32_t c1 = 0, c2 = 0;
+        for (uint32_t cs = dv & ~31u; dv && cs <= dv; cs -= 32) {   // blocks from the last one down
+            const uint32_t k = cs + lane;
+            const uint32_t e = k < dv ? adj[ob + k] : 0u;
+            const uint32_t b1 = __ballot_sync(0xffffffffu, (e & 3u) == 1u);
+            const uint32_t b2 = __ballot_sync(0xffffffffu, (e & 3u) == 2u);
+            if (k < lv) {
+                const uint32_t u = e >> 2;
+                uint64_t lo = off[u] + up[u], hi = off[u + 1];
+                while (lo < hi) {
+                    const uint64_t mid = (lo + hi) >> 1;
+                    if ((adj[mid] >> 2) < (uint32_t)v) lo = mid + 1; else hi = mid;
+                }
+                const uint64_t idx = ub[u] + (lo - off[u] - up[u]);
+                rp[idx] = k;
+                vs[idx] = make_uint2(c1 + __popc(b1 & after), c2 + __popc(b2 & after));
+                walk += dv - k - 1;
+            }
+            c1 += __popc(b1);
+            c2 += __popc(b2);
+            if (cs == 0) break;
+        }
+    }
+    for (int o = 16; o; o >>= 1) walk += __shfl_xor_sync(0xffffffffu, walk, o);
+    if (lane == 0 && walk) atomicAdd(wk, walk);
+}
+
+// upper pairs per vertex: deg - up
+__global__ void k_upper_of(const uint64_t* off, const uint32_t* up, uint32_t n, uint32_t* cnt) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x)
+        cnt[x] = (uint32_t)(off[x + 1] - off[x]) - up[x];
+}
+
 // ---- CSR input validation: stats[6] = number of violations
 __global__ void k_check_csr(const uint64_t* off, const uint32_t* adj, uint32_t n, uint64_t total,
                             unsigned long long* stats) {
@@ -263,9 +313,32 @@ tc_status finish_graph(GraphStore& g, uint64_t E, int B, uint64_t* ukey, uint32_
     k_graph_sums<<<gridN, kB, 0, st>>>(g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(), n,
                                        stats.as<unsigned long long>());
     TC_LAUNCH("k_graph_sums");
+    // per upper pair tables: ub = exclusive scan of the upper pairs per vertex
+    {
+        DevBuf ucnt;
+        TC_TRY(ucnt.alloc(sizeof(uint32_t) * (n ? n : 1), st));
+        TC_TRY(g.ub.alloc_persistent(sizeof(uint64_t) * (n + 1ull)));
+        TC_TRY(g.rp.alloc_persistent(sizeof(uint32_t) * (E ? E : 1)));
+        TC_TRY(g.vs.alloc_persistent(sizeof(uint2) * (E ? E : 1)));
+        if (n) {
+            k_upper_of<<<gridN, kB, 0, st>>>(g.off.as<uint64_t>(), g.up.as<uint32_t>(), n, ucnt.as<uint32_t>());
+            TC_LAUNCH("k_upper_of");
+        }
+        TC_TRY(scan_u32_to_u64(ucnt.as<uint32_t>(), g.ub.as<uint64_t>(), n, st));
+        if (E) {
+            // the walk length goes to stats[1] (ids out of range), which is zero here: a build with
+            // such ids stops before this point
+            k_pair_tables<<<grid_for((uint64_t)n * 32, kB, 1u << 16), kB, 0, st>>>(
+                g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(),
+                                                g.ub.as<uint64_t>(), n, g.rp.as<uint32_t>(), g.vs.as<uint2>(),
+                                                stats.as<unsigned long long>() + 1);
+            TC_LAUNCH("k_pair_tables");
+        }
+    }
     unsigned long long hs[8];
     TC_CUDA(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaStreamSynchronize(st));
+    g.sum_walk = hs[1];
     g.e_sym = E;
     g.mutual = hs[2];
     g.arcs = E + hs[2];

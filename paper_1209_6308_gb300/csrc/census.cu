@@ -151,15 +151,28 @@ __device__ __forceinline__ void pk_maybe_flush(Counts& k, int lane) {
 // per dir(u,w) class (packed 21-bit fields; 0 for the union walk, which counts them one by
 // one), dy the dyadic base n - d_u - d_v (0 after the pair's first chunk); the common
 // neighbours complete the dyadic count n - |S| - 2 (steps 2.1.2 - 2.1.3).
+// VT (per-pair tables): the walk covers only the w > u of N[v], vo holds the common
+// neighbours by dir(v,w), and vsv = (class-1 count, class-2 count, length) of N[v] past u (zero
+// except in the pair's first fold), so the v-only triads are the suffix counts minus vo (mod
+// 2^64 across folds); the common neighbours w < u of the pair were credited by the pairs
+// (w, u) that met this pair's triangle, so the dyadic count takes only the walked ones.
+template <bool VT>
 __device__ __forceinline__ void pair_fold(Counts& k, PairAcc& pa, int lane, uint32_t duv, uint32_t cuv,
-                                          const uint8_t* sT, unsigned long long suf, unsigned long long dy) {
-    const uint32_t cm = __reduce_add_sync(0xffffffffu, pa.cm);
+                                          const uint8_t* sT, unsigned long long suf, unsigned long long dy,
+                                          uint3 vsv = make_uint3(0u, 0u, 0u)) {
+    uint32_t cm = VT ? 0u : __reduce_add_sync(0xffffffffu, pa.cm);
 #pragma unroll
     for (uint32_t d = 1; d <= 3; ++d) {
         const uint32_t vs = __reduce_add_sync(0xffffffffu, (uint32_t)((pa.vo >> (16 * d)) & 0xffffull));
         const uint32_t fs = __reduce_add_sync(0xffffffffu, (uint32_t)((pa.fo >> (16 * d)) & 0xffffull));
         const int cv = sT[cuv | (d << 2)], cu = sT[cuv | (d << 4)];
-        if (lane == cv) k.racc += vs;
+        if (VT) {
+            cm += vs;
+            const uint32_t tot = d == 1 ? vsv.x : d == 2 ? vsv.y : vsv.z - vsv.x - vsv.y;
+            if (lane == cv) k.racc += (unsigned long long)tot - (unsigned long long)vs;
+        } else {
+            if (lane == cv) k.racc += vs;
+        }
         if (lane == cu) k.racc += ((suf >> (21 * (d - 1))) & 0x1fffffull) - (unsigned long long)fs;
     }
     if (lane == (duv == 3u ? 2 : 1)) k.racc += dy + cm;
@@ -185,6 +198,10 @@ __device__ __forceinline__ void load_trip(uint32_t (&x)[kUnroll], const uint32_t
 //   found:  a common neighbour; counts toward |N[u] n N[v]| and, past v, is a triad with both
 //           links (its u-only count from the u side is taken back);
 //   else:   reached through v only; kept when w > u (the canonical rule of step 2.1.4).
+// VT: every entry walked is past u; a common neighbour is counted by dir(v,w) (the v-only
+// triads come from the pair's suffix counts), and one past v also credits the pair (v, w)
+// with the common neighbour u, in the dyadic class of dir(v,w).
+template <bool VT>
 __device__ __forceinline__ void classify_trip(const uint32_t (&cur)[kUnroll], const uint32_t* sH, int hb,
                                               uint32_t hmask, uint32_t u, uint32_t v, uint32_t cuv,
                                               const uint8_t* sT, Counts& k, PairAcc& pa) {
@@ -204,7 +221,17 @@ __device__ __forceinline__ void classify_trip(const uint32_t (&cur)[kUnroll], co
 #pragma unroll
     for (int r = 0; r < kUnroll; ++r) {
         const uint32_t x = cur[r] >> 2, dvw = cur[r] & 3u;
-        if (e[r] != kEmpty) {
+        if (VT) {
+            if (e[r] != kEmpty) {
+                pa.vo += 1ull << (dvw << 4);
+                if (x > v) {
+                    const uint32_t duw = e[r] & 3u;
+                    pk_add(k, sT[cuv | (dvw << 2) | (duw << 4)]);
+                    pa.fo += 1ull << (duw << 4);
+                    pk_add(k, dvw == 3u ? 2u : 1u);
+                }
+            }
+        } else if (e[r] != kEmpty) {
             ++pa.cm;
             if (x > v) {
                 const uint32_t duw = e[r] & 3u;
@@ -222,6 +249,7 @@ __device__ __forceinline__ void classify_trip(const uint32_t (&cur)[kUnroll], co
 // The v side of one pair (u, v) in a chunked hub: every w of N[v] from position k0 up to the
 // chunk's id bound is looked up in the staged hash of N[u].  Returns the position after the
 // last entry taken.
+template <bool VT>
 __device__ __forceinline__ uint32_t v_side_chunk(const uint32_t* __restrict__ B, uint32_t k0, uint32_t dv,
                                                  uint32_t hi_key, const uint32_t* sH, int hb, uint32_t hmask,
                                                  uint32_t u, uint32_t v, uint32_t duv, uint32_t cuv, const uint8_t* sT,
@@ -230,9 +258,9 @@ __device__ __forceinline__ uint32_t v_side_chunk(const uint32_t* __restrict__ B,
     load_trip<true>(cur, B, k0, dv, hi_key, lane);
     for (;;) {
         pk_maybe_flush(k, lane);
-        if (pa.trips >= kPairSpillTrips) pair_fold(k, pa, lane, duv, cuv, sT, 0ull, 0ull);
+        if (pa.trips >= kPairSpillTrips) pair_fold<VT>(k, pa, lane, duv, cuv, sT, 0ull, 0ull);
         load_trip<true>(nxt, B, k0 + kTrip, dv, hi_key, lane);
-        classify_trip(cur, sH, hb, hmask, u, v, cuv, sT, k, pa);
+        classify_trip<VT>(cur, sH, hb, hmask, u, v, cuv, sT, k, pa);
         uint32_t taken = 0;
 #pragma unroll
         for (int r = 0; r < kUnroll; ++r) taken += __popc(__ballot_sync(0xffffffffu, cur[r] != 0u));
@@ -251,7 +279,9 @@ __device__ __forceinline__ void flush_graph(Counts& k, int lane, unsigned long l
     k.racc = 0;
 }
 
-template <int ALGO, int MODE = kModeSingle>
+// VT: the graphs carry the per upper pair tables (GraphDev::ub, rp, vs): each N[v] walk starts
+// past u, and the v-only triads come from the tables' suffix counts.
+template <int ALGO, int MODE, bool VT>
 __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t chunk = P.chunk;
@@ -282,6 +312,9 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     const uint64_t* __restrict__ off = P.g.off;
     const uint32_t* __restrict__ adj = P.g.adj;
     const uint32_t* __restrict__ upv = P.g.up;
+    const uint64_t* __restrict__ ubp = P.g.ub;
+    const uint32_t* __restrict__ rpp = P.g.rp;
+    const uint2* __restrict__ vsp = P.g.vs;
     uint32_t cur_graph = 0xffffffffu;          // batched: the graph whose totals the lanes hold
     unsigned long long* gout = P.out;
     Counts cnt;
@@ -298,6 +331,9 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
         off = G.off;
         adj = G.adj;
         upv = G.up;
+        ubp = G.ub;
+        rpp = G.rp;
+        vsp = G.vs;
         gout = MODE == kModeWave ? sReq[gi].out : P.out + 16ull * gi;
     };
 
@@ -323,8 +359,10 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
         const uint32_t nchunks = (du + chunk - 1) / chunk;
         const uint32_t npairs = w.j1 - w.j0;                      // <= kMaxItemPairs
         const uint32_t G = max(1u, min(32u, npairs / (4u * kWarps)));
+        // table index of the item's first pair
+        const uint64_t pb = VT ? ubp[u] + (w.j0 - upv[u]) : 0ull;
         if (nchunks > 1)
-            for (uint32_t i = tid; i < npairs; i += kThreads) sCur[i] = 0;
+            for (uint32_t i = tid; i < npairs; i += kThreads) sCur[i] = VT ? rpp[pb + i] + 1u : 0u;
 
         for (uint32_t c = 0; c < nchunks; ++c) {
             const uint32_t a0 = c * chunk, a1 = min(du, a0 + chunk), LA = a1 - a0;
@@ -388,6 +426,13 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                 const uint64_t vb_l = okl ? off[euv_l >> 2] : 0ull;
                 const uint32_t dv_l = okl ? (uint32_t)(off[(euv_l >> 2) + 1] - vb_l) : 0u;
                 const uint32_t cur_l = (okl && nchunks > 1) ? sCur[base + lane] : 0u;
+                // tables of the grabbed pairs, needed for their first chunk
+                uint32_t rp_l = 0;
+                uint2 vs_l = make_uint2(0u, 0u);
+                if (VT && c == 0 && okl) {
+                    rp_l = rpp[pb + base + lane];
+                    vs_l = vsp[pb + base + lane];
+                }
                 // u side of pair t of this grab and the fold of its counts
                 auto finish_pair = [&](uint32_t t, uint32_t duv, uint32_t cuv, uint32_t dv) {
                     const uint32_t j = w.j0 + base + t;
@@ -407,7 +452,13 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                         const uint32_t bl = r ? (sLo[q] & m) : 0u, bh = r ? (sHi[q] & m) : 0u;
                         suf = sCk[nq] - sCk[q] - pack3(__popc(bl & ~bh), __popc(bh & ~bl), __popc(bl & bh));
                     }
-                    pair_fold(cnt, pa, lane, duv, cuv, sT, suf, c == 0 ? n - du - dv : 0ull);
+                    uint3 vsv = make_uint3(0u, 0u, 0u);
+                    if (VT && c == 0) {
+                        vsv.x = __shfl_sync(0xffffffffu, vs_l.x, t);
+                        vsv.y = __shfl_sync(0xffffffffu, vs_l.y, t);
+                        vsv.z = dv - 1u - __shfl_sync(0xffffffffu, rp_l, t);
+                    }
+                    pair_fold<VT>(cnt, pa, lane, duv, cuv, sT, suf, c == 0 ? n - du - dv : 0ull, vsv);
                 };
                 if (has_hi) {
                     // chunked hub: each pair resumes at its cursor and stops at the chunk's id bound
@@ -417,15 +468,21 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                         const uint32_t dv = __shfl_sync(0xffffffffu, dv_l, t);
                         const uint32_t start = __shfl_sync(0xffffffffu, cur_l, t);
                         const uint32_t v = euv >> 2, duv = euv & 3u, cuv = code_uv(duv);
-                        const uint32_t kend =
-                            v_side_chunk(adj + vb, start, dv, hi_key, sH, hb, hmask, u, v, duv, cuv, sT, cnt, pa, lane);
+                        const uint32_t kend = v_side_chunk<VT>(adj + vb, start, dv, hi_key, sH, hb, hmask, u, v, duv, cuv,
+                                                               sT, cnt, pa, lane);
                         if (lane == 0) sCur[base + t] = kend;
                         finish_pair(t, duv, cuv, dv);
                     }
                 } else {
                     // the rest of each N[v]: one flattened (pair, trip) loop whose next trip's
                     // loads, possibly of the next pair, are in flight while this one is classified
-                    uint32_t t = 0, k0 = nchunks > 1 ? __shfl_sync(0xffffffffu, cur_l, 0) : 0u;
+                    // each pair's walk starts at its cursor (hub chunks), past u (tables) or at 0
+                    auto start_of = [&](uint32_t q) -> uint32_t {
+                        if (nchunks > 1) return __shfl_sync(0xffffffffu, cur_l, q);
+                        if (VT) return __shfl_sync(0xffffffffu, rp_l, q) + 1u;
+                        return 0u;
+                    };
+                    uint32_t t = 0, k0 = start_of(0);
                     uint32_t euv = __shfl_sync(0xffffffffu, euv_l, 0);
                     uint64_t vb = __shfl_sync(0xffffffffu, vb_l, 0);
                     uint32_t dv = __shfl_sync(0xffffffffu, dv_l, 0);
@@ -434,11 +491,11 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                     for (;;) {
                         pk_maybe_flush(cnt, lane);
                         const uint32_t v = euv >> 2, duv = euv & 3u, cuv = code_uv(duv);
-                        if (pa.trips >= kPairSpillTrips) pair_fold(cnt, pa, lane, duv, cuv, sT, 0ull, 0ull);
+                        if (pa.trips >= kPairSpillTrips) pair_fold<VT>(cnt, pa, lane, duv, cuv, sT, 0ull, 0ull);
                         uint32_t nt = t, nk0 = k0 + kTrip;
                         if (nk0 >= dv) {
                             nt = t + 1;
-                            nk0 = (nchunks > 1 && nt < np) ? __shfl_sync(0xffffffffu, cur_l, nt) : 0u;
+                            nk0 = nt < np ? start_of(nt) : 0u;
                         }
                         const bool more = nt < np;
                         uint32_t neuv = euv, ndv = dv;
@@ -449,7 +506,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                             ndv = __shfl_sync(0xffffffffu, dv_l, nt);
                         }
                         if (more) load_trip<false>(nxt, adj + nvb, nk0, ndv, 0u, lane);
-                        classify_trip(cur, sH, hb, hmask, u, v, cuv, sT, cnt, pa);
+                        classify_trip<VT>(cur, sH, hb, hmask, u, v, cuv, sT, cnt, pa);
                         if (nt != t) {
                             if (nchunks > 1 && lane == 0) sCur[base + t] = dv;
                             finish_pair(t, duv, cuv, dv);
@@ -516,6 +573,13 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                 const uint32_t euv_l = okl ? wA[jl] : 0u;
                 const uint64_t vb_l = okl ? off[euv_l >> 2] : 0ull;
                 const uint32_t dv_l = okl ? (uint32_t)(off[(euv_l >> 2) + 1] - vb_l) : 0u;
+                uint32_t rp_l = 0;
+                uint2 vs_l = make_uint2(0u, 0u);
+                if (VT && okl) {
+                    const uint64_t ti = ubp[u] + (jl - p0);
+                    rp_l = rpp[ti];
+                    vs_l = vsp[ti];
+                }
                 const uint32_t np = min(32u, du - jb);
                 for (uint32_t t = 0; t < np; ++t) {
                     const uint32_t euv = __shfl_sync(0xffffffffu, euv_l, t);
@@ -524,9 +588,16 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                     const uint32_t v = euv >> 2, duv = euv & 3u, cuv = code_uv(duv);
                     const uint32_t* __restrict__ B = adj + vb;
                     const uint32_t j = jb + t;
-                    for (uint32_t kb = 0; kb < dv; kb += 32) {
+                    uint3 vsv = make_uint3(0u, 0u, 0u);
+                    uint32_t kstart = 0;
+                    if (VT) {
+                        kstart = __shfl_sync(0xffffffffu, rp_l, t) + 1u;
+                        vsv = make_uint3(__shfl_sync(0xffffffffu, vs_l.x, t), __shfl_sync(0xffffffffu, vs_l.y, t),
+                                         dv - kstart);
+                    }
+                    for (uint32_t kb = kstart; kb < dv; kb += 32) {
                         pk_maybe_flush(cnt, lane);
-                        if (pa.trips >= kPairSpillTrips) pair_fold(cnt, pa, lane, duv, cuv, sT, 0ull, 0ull);
+                        if (pa.trips >= kPairSpillTrips) pair_fold<VT>(cnt, pa, lane, duv, cuv, sT, 0ull, 0ull);
                         const uint32_t k = kb + lane;
                         if (k < dv) {
                             const uint32_t xe = __ldg(B + k), x = xe >> 2, dvw = xe & 3u;
@@ -536,13 +607,15 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                                 if ((wA[mid] >> 2) < x) lo = mid + 1; else hi = mid;
                             }
                             if (lo < du && (wA[lo] >> 2) == x) {
-                                ++pa.cm;
+                                if (VT) pa.vo += 1ull << (dvw << 4);
+                                else ++pa.cm;
                                 if (x > v) {
                                     const uint32_t duw = wA[lo] & 3u;
                                     pk_add(cnt, sT[cuv | (dvw << 2) | (duw << 4)]);
                                     pa.fo += 1ull << (duw << 4);
+                                    if (VT) pk_add(cnt, dvw == 3u ? 2u : 1u);
                                 }
-                            } else if (x > u) {
+                            } else if (!VT && x > u) {
                                 pa.vo += 1ull << (dvw << 4);
                             }
                         }
@@ -563,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                             suf += ballot3((k > j && k < du) ? (wA[k] & 3u) : 0u);
                         }
                     }
-                    pair_fold(cnt, pa, lane, duv, cuv, sT, suf, n - du - dv);
+                    pair_fold<VT>(cnt, pa, lane, duv, cuv, sT, suf, n - du - dv, vsv);
                 }
             }
             if (!MULTI && P.vcost && lane == 0) P.vcost[u] += (unsigned long long)(clock64() - t_vert);
@@ -633,8 +706,9 @@ __global__ void k_plan_emit(GraphDev g, uint32_t u_end, const uint32_t* pos, con
 }
 
 std::atomic<uint64_t> g_table_uploaded{0};
-std::atomic<uint64_t> g_attr_set[6] = {{0}, {0}, {0}, {0}, {0}, {0}};
-std::atomic<int> g_dyn_limit[6] = {{0}, {0}, {0}, {0}, {0}, {0}};   // per kernel form: optin - static smem
+constexpr int kForms = 4;   // single graph without tables, single graph, batch, wave (all with tables)
+std::atomic<uint64_t> g_attr_set[2 * kForms] = {};
+std::atomic<int> g_dyn_limit[2 * kForms] = {};   // per kernel form: optin - static smem
 
 size_t census_smem(uint32_t algo, uint32_t chunk) {
     return sizeof(uint32_t) * (algo == TC_ALGO_UNION ? 3ull : 4ull) * chunk + sizeof(uint32_t) * (chunk / 16) +
@@ -657,10 +731,12 @@ tc_status prepare_device(cudaStream_t st, int algo, size_t smem) {
     TC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int limit = optin - 256;   // leave room for the kernel's static shared variables
     if ((int)smem > limit) return fail(TC_ERR_ARG, "chunk_entries too large for this GPU's shared memory");
-    const void* fns[6] = {(const void*)k_census<TC_ALGO_UNION, kModeSingle>, (const void*)k_census<TC_ALGO_SUFFIX, kModeSingle>,
-                          (const void*)k_census<TC_ALGO_UNION, kModeBatch>, (const void*)k_census<TC_ALGO_SUFFIX, kModeBatch>,
-                          (const void*)k_census<TC_ALGO_UNION, kModeWave>, (const void*)k_census<TC_ALGO_SUFFIX, kModeWave>};
-    for (int b = 0; b < 3; ++b) {
+    const void* fns[2 * kForms] = {
+        (const void*)k_census<TC_ALGO_UNION, kModeSingle, false>, (const void*)k_census<TC_ALGO_SUFFIX, kModeSingle, false>,
+        (const void*)k_census<TC_ALGO_UNION, kModeSingle, true>,  (const void*)k_census<TC_ALGO_SUFFIX, kModeSingle, true>,
+        (const void*)k_census<TC_ALGO_UNION, kModeBatch, true>,   (const void*)k_census<TC_ALGO_SUFFIX, kModeBatch, true>,
+        (const void*)k_census<TC_ALGO_UNION, kModeWave, true>,    (const void*)k_census<TC_ALGO_SUFFIX, kModeWave, true>};
+    for (int b = 0; b < kForms; ++b) {
         const int idx = 2 * b + algo;
         if (!(g_attr_set[idx].load() & bit)) {
             // dynamic + static shared memory may not exceed the opt-in limit; the wave form
@@ -754,8 +830,8 @@ tc_status census_launch_batch(const GraphDev* d_graphs, const Item* items, uint3
     P.wblocks = wblocks;
     P.n_wblocks = n_wblocks;
     const unsigned grid = (unsigned)census_grid(o);
-    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, kModeBatch><<<grid, kThreads, smem, st>>>(P);
-    else k_census<TC_ALGO_SUFFIX, kModeBatch><<<grid, kThreads, smem, st>>>(P);
+    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, kModeBatch, true><<<grid, kThreads, smem, st>>>(P);
+    else k_census<TC_ALGO_SUFFIX, kModeBatch, true><<<grid, kThreads, smem, st>>>(P);
     TC_LAUNCH("k_census (batched)");
     return TC_OK;
 }
@@ -774,8 +850,8 @@ tc_status census_launch_wave(const WaveReq* d_reqs, uint32_t n_reqs, uint32_t to
     P.n_wblocks = total_blocks;
     P.reqs = d_reqs;
     P.n_reqs = n_reqs;
-    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, kModeWave><<<grid, kThreads, smem, st>>>(P);
-    else k_census<TC_ALGO_SUFFIX, kModeWave><<<grid, kThreads, smem, st>>>(P);
+    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, kModeWave, true><<<grid, kThreads, smem, st>>>(P);
+    else k_census<TC_ALGO_SUFFIX, kModeWave, true><<<grid, kThreads, smem, st>>>(P);
     TC_LAUNCH("k_census (wave)");
     return TC_OK;
 }
@@ -805,8 +881,14 @@ tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items
     P.reqs = nullptr;
     P.n_reqs = 0;
     const unsigned grid = (unsigned)census_grid(o);
-    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION><<<grid, kThreads, smem, st>>>(P);
-    else k_census<TC_ALGO_SUFFIX><<<grid, kThreads, smem, st>>>(P);
+    const bool vt = P.g.vs != nullptr;
+    if (o.algo == TC_ALGO_UNION) {
+        if (vt) k_census<TC_ALGO_UNION, kModeSingle, true><<<grid, kThreads, smem, st>>>(P);
+        else k_census<TC_ALGO_UNION, kModeSingle, false><<<grid, kThreads, smem, st>>>(P);
+    } else {
+        if (vt) k_census<TC_ALGO_SUFFIX, kModeSingle, true><<<grid, kThreads, smem, st>>>(P);
+        else k_census<TC_ALGO_SUFFIX, kModeSingle, false><<<grid, kThreads, smem, st>>>(P);
+    }
     TC_LAUNCH("k_census");
     return TC_OK;
 }
@@ -838,8 +920,14 @@ tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream
     P.reqs = nullptr;
     P.n_reqs = 0;
     const unsigned grid = (unsigned)census_grid(o);
-    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION><<<grid, kThreads, smem, st>>>(P);
-    else k_census<TC_ALGO_SUFFIX><<<grid, kThreads, smem, st>>>(P);
+    const bool vt = P.g.vs != nullptr;
+    if (o.algo == TC_ALGO_UNION) {
+        if (vt) k_census<TC_ALGO_UNION, kModeSingle, true><<<grid, kThreads, smem, st>>>(P);
+        else k_census<TC_ALGO_UNION, kModeSingle, false><<<grid, kThreads, smem, st>>>(P);
+    } else {
+        if (vt) k_census<TC_ALGO_SUFFIX, kModeSingle, true><<<grid, kThreads, smem, st>>>(P);
+        else k_census<TC_ALGO_SUFFIX, kModeSingle, false><<<grid, kThreads, smem, st>>>(P);
+    }
     TC_LAUNCH("k_census");
     return TC_OK;
 }

@@ -49,6 +49,13 @@ uint64_t steady_ns() {
 
 constexpr uint64_t kPairUnits = 16;   // per-pair overhead in element units (offsets, the pair fold)
 
+// N[v] entries the census walks for the upper pair (u, v = N[u][j]): those past u when the
+// graph has per-pair tables, else all of N[v].
+__device__ __forceinline__ uint64_t walked(const GraphDev& g, uint32_t u, uint32_t j, uint32_t v) {
+    const uint64_t dv = g.off[v + 1] - g.off[v];
+    return g.rp ? dv - 1 - g.rp[g.ub[u] + (j - g.up[u])] : dv;
+}
+
 // Cost of CTA item i in element units: staging N[u] once, then N[v] plus a fixed overhead per
 // pair and per pair and chunk of N[u] (the pair's cursor), and the union walk's u side, which
 // visits about half of N[u] per pair.  One warp per item.
@@ -63,7 +70,7 @@ __global__ void k_item_cost(GraphDev g, const Item* __restrict__ items, uint32_t
         unsigned long long c = 0;
         for (uint32_t j = it.j0 + lane; j < it.j1; j += 32) {
             const uint32_t v = g.adj[ub + j] >> 2;
-            c += (g.off[v + 1] - g.off[v]) + kPairUnits + (algo == TC_ALGO_UNION ? du / 2 : 0);
+            c += walked(g, it.u, j, v) + kPairUnits + (algo == TC_ALGO_UNION ? du / 2 : 0);
         }
         c = __reduce_add_sync(0xffffffffu, (unsigned)(c & 0xffffffffu)) +
             ((unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)(c >> 32)) << 32);
@@ -86,7 +93,7 @@ __global__ void k_block_cost(GraphDev g, uint32_t w0, uint32_t w1, uint32_t n_bl
             c = du;
             for (uint64_t j = ub + g.up[u]; j < ub + du; ++j) {
                 const uint32_t v = g.adj[j] >> 2;
-                c += (g.off[v + 1] - g.off[v]) + kPairUnits + (algo == TC_ALGO_UNION ? du / 2 : 0);
+                c += walked(g, (uint32_t)u, (uint32_t)(j - ub), v) + kPairUnits + (algo == TC_ALGO_UNION ? du / 2 : 0);
             }
         }
         c = __reduce_add_sync(0xffffffffu, (unsigned)(c & 0xffffffffu)) +
@@ -679,7 +686,8 @@ tc_status tc_server_add_graph(tc_server* s, tc_graph* g, void* stream, uint32_t*
     G->warp_end = p->warp_end;
     G->n_blocks = (p->warp_end - p->warp_begin + 31) / 32;
     const uint64_t item_bytes = sizeof(Item) * (uint64_t)std::max(p->n_items, 1u);
-    G->bytes = g->s.off.bytes + g->s.adj.bytes + g->s.up.bytes + g->s.new_of_old.bytes + item_bytes;
+    G->bytes = g->s.off.bytes + g->s.adj.bytes + g->s.up.bytes + g->s.new_of_old.bytes + g->s.ub.bytes +
+               g->s.rp.bytes + g->s.vs.bytes + item_bytes;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->resident + G->bytes > s->budget) {
