@@ -39,7 +39,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kEmpty = 0u;              // stored entries always have dir != 0
 #ifndef TC_UNROLL
-#define TC_UNROLL 4
+#define TC_UNROLL 3
 #endif
 #ifndef TC_MIN_BLOCKS
 #define TC_MIN_BLOCKS 3
