@@ -29,7 +29,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "triad-census arcs/sec (bit-exact), learned/batched vs plain; % HBM roofline"
-WORKLOAD = dict(name="rmat20_ef16_r20_seed2", scale=20, edge_factor=16, recip=0.2, seed=2)
+# R-MAT workloads by scale (edge factor 16, a/b/c = .57/.19/.19, ids permuted): scale 20 is the
+# bench's default; scale 10 the small parity case; scale 26 the learned-vs-plain comparison
+WORKLOADS = {10: dict(name="rmat10_ef16_r15_seed1", scale=10, edge_factor=16, recip=0.15, seed=1),
+             20: dict(name="rmat20_ef16_r20_seed2", scale=20, edge_factor=16, recip=0.2, seed=2),
+             26: dict(name="rmat26_ef16_r20_seed3", scale=26, edge_factor=16, recip=0.2, seed=3)}
+WORKLOAD = dict(WORKLOADS[20])
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_census_rmat20_traffic.txt")
 CENSUS_SRC = os.path.join(ROOT, "paper_1209_6308_gb300", "csrc", "census.cu")
 
@@ -51,7 +56,11 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=20.0, help="measured seconds per serving arm")
     p.add_argument("--serve-warmup", type=float, default=5.0, help="unmeasured seconds before them")
     p.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
-    return p.parse_args()
+    p.add_argument("--scale", type=int, default=20, choices=sorted(WORKLOADS), help="R-MAT workload scale")
+    a = p.parse_args()
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[a.scale])
+    return a
 
 
 def workload():
@@ -279,8 +288,9 @@ def learned_comparison(tc, g, stream, model, info):
     (identical counts required) and the held-out cost-prediction error of both."""
     from paper_1209_6308_gb300 import learned
     learned.attach(model, g, stream=stream.cuda_stream)
-    plain_ms, plain_c = learned.census_ms(g, learned.PLAIN, stream)
-    learned_ms, learned_c = learned.census_ms(g, learned.LEARNED, stream)
+    reps = 5 if g.n <= (1 << 22) else 3
+    plain_ms, plain_c = learned.census_ms(g, learned.PLAIN, stream, reps=reps)
+    learned_ms, learned_c = learned.census_ms(g, learned.LEARNED, stream, reps=reps)
     q = learned.prediction_quality(model, g, stream=stream.cuda_stream)
     return {"training": info, "plain_ms": plain_ms, "learned_ms": learned_ms,
             "speedup": plain_ms / learned_ms, "counts_identical": plain_c == learned_c,
@@ -465,8 +475,9 @@ def run_gpu(args):
     counts[0] = tc.tc_null_count(n, counts)
 
     # end to end through the C ABI from pinned host buffers
-    src_pin = torch.from_numpy(s.view("int32")).pin_memory()
-    dst_pin = torch.from_numpy(d.view("int32")).pin_memory()
+    if args.e2e_steps > 0:
+        src_pin = torch.from_numpy(s.view("int32")).pin_memory()
+        dst_pin = torch.from_numpy(d.view("int32")).pin_memory()
     learned_line = None
     model = None
     if not args.no_learned and rank == 0:

@@ -61,6 +61,16 @@ def test_defaults_finish_in_minutes(monkeypatch):
     assert a.impl == "ours" and a.serve_seconds <= 30
 
 
+@pytest.mark.parametrize("argv,scale", [([], 20), (["--scale", "26"], 26), (["--scale", "10"], 10), ([], 20)])
+def test_workload_follows_the_scale_option(monkeypatch, argv, scale):
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
+    bench.parse()
+    assert bench.WORKLOAD["scale"] == scale
+    assert bench.WORKLOAD == bench.WORKLOADS[scale] and bench.WORKLOAD is not bench.WORKLOADS[scale]
+    assert bench.WORKLOADS[20]["name"] == "rmat20_ef16_r20_seed2"
+
+
 def test_reference_arm_on_other_ranks_exits_without_work(monkeypatch):
     import bench
     monkeypatch.setenv("RANK", "1")
