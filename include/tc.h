@@ -274,7 +274,8 @@ typedef struct {
     uint32_t quantum_us;      /* target device time of one wave (0 = 1000) */
     uint32_t lanes;           /* CUDA streams waves are issued on, 1..4 (0 = 3): one bulk lane, the rest express */
     uint32_t starve_ms;       /* age after which a request is served before all younger ones (0 = 50) */
-    uint32_t reserved[9];
+    uint32_t max_item_units;  /* work items above max(this, 4 deg(u)) cost units are split for serving (0 = 2^20) */
+    uint32_t reserved[8];
 } tc_server_options;
 
 typedef struct {

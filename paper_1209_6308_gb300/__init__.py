@@ -57,7 +57,7 @@ class tc_graph_info(ctypes.Structure):
 class tc_server_options(ctypes.Structure):
     _fields_ = [("census", tc_options), ("budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_uint32),
                 ("max_pending", ctypes.c_uint32), ("quantum_us", ctypes.c_uint32), ("lanes", ctypes.c_uint32),
-                ("starve_ms", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 9)]
+                ("starve_ms", ctypes.c_uint32), ("max_item_units", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 8)]
 
 
 class tc_serve_result(ctypes.Structure):

@@ -102,6 +102,26 @@ __global__ void k_block_cost(GraphDev g, uint32_t w0, uint32_t w1, uint32_t n_bl
     }
 }
 
+// Cost of every pair of the listed items (pair p of the concatenation: item it[q] with
+// pre[q] <= p < pre[q+1]), in the units of k_item_cost without the item's staging term.
+__global__ void k_pair_cost(GraphDev g, const Item* __restrict__ items, const uint32_t* __restrict__ it,
+                            const uint64_t* __restrict__ pre, uint32_t nq, uint64_t total, int algo, uint32_t chunk,
+                            unsigned long long* cost) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < total; p += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = nq;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (pre[mid] <= p) lo = mid; else hi = mid;
+        }
+        const Item w = items[it[lo]];
+        const uint32_t j = w.j0 + (uint32_t)(p - pre[lo]);
+        const uint64_t ub = g.off[w.u], du = g.off[w.u + 1] - ub;
+        const uint32_t v = g.adj[ub + j] >> 2;
+        cost[p] = walked(g, w.u, j, v) + kPairUnits + ((du + chunk - 1) / chunk) * kPairUnits +
+                  (algo == TC_ALGO_UNION ? du / 2 : 0);
+    }
+}
+
 // Copy the finished requests' counters to host memory and zero their slots for reuse.
 struct CollectArgs {
     unsigned long long* src[kMaxWave];
@@ -180,6 +200,7 @@ struct tc_server {
     uint64_t budget = 0, resident = 0;
     uint32_t max_active = 1024, max_pending = 65536, lanes_n = 2;
     uint64_t quantum_ns = 1000000, starve_ns = 50000000;
+    uint64_t max_item_units = 1u << 20;
     int device = 0;
     unsigned grid = 0;          // census grid (every CTA slot)
     unsigned grid_bulk = 0;     // bulk-lane waves when express lanes exist
@@ -623,6 +644,7 @@ tc_status tc_server_create(const tc_server_options* opt, tc_server** out) {
     s->lanes_n = o.lanes ? o.lanes : 3;
     s->quantum_ns = (uint64_t)(o.quantum_us ? o.quantum_us : 1000) * 1000ull;
     s->starve_ns = (uint64_t)(o.starve_ms ? o.starve_ms : 50) * 1000000ull;
+    s->max_item_units = o.max_item_units ? o.max_item_units : (1u << 20);
     TC_CUDA(cudaGetDevice(&s->device));
     size_t fr = 0, total = 0;
     TC_CUDA(cudaMemGetInfo(&fr, &total));
@@ -724,6 +746,94 @@ tc_status tc_server_add_graph(tc_server* s, tc_graph* g, void* stream, uint32_t*
                             cudaSuccess) ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return unreserve(cuda_fail(cudaGetLastError(), "cost of the work plan"));
+    // A wave lasts as long as its heaviest item, and the plan splits a hub's pairs evenly by
+    // count, so its first items (the pairs with other hubs) can be far heavier than the rest.
+    // Items above max(max_item_units, 4 deg(u)) units are cut into consecutive pair ranges by
+    // their pairs' exact costs; every piece stages N[u] again, which the floor of 4 deg(u)
+    // keeps to a quarter of a piece at most.
+    std::vector<uint32_t> heavy;
+    std::vector<Item> hitems;
+    if (G->n_items) {
+        hitems.resize(G->n_items);
+        if (cudaMemcpyAsync(hitems.data(), G->items.p, sizeof(Item) * G->n_items, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return unreserve(cuda_fail(cudaGetLastError(), "copy of the work plan"));
+    }
+    for (uint32_t i = 0; i < G->n_items; ++i)
+        if (hitems[i].j1 - hitems[i].j0 > 1 && hi[i] > s->max_item_units) heavy.push_back(i);
+    if (!heavy.empty()) {
+        std::vector<uint64_t> qpre(heavy.size() + 1, 0);
+        for (size_t q = 0; q < heavy.size(); ++q) qpre[q + 1] = qpre[q] + (hitems[heavy[q]].j1 - hitems[heavy[q]].j0);
+        const uint64_t total = qpre.back();
+        DevBuf d_it, d_pre, d_pc;
+        if (d_it.alloc(sizeof(uint32_t) * heavy.size(), st) != TC_OK || d_pre.alloc(sizeof(uint64_t) * qpre.size(), st) != TC_OK ||
+            d_pc.alloc(sizeof(unsigned long long) * total, st) != TC_OK)
+            return unreserve(TC_ERR_OOM);
+        std::vector<uint64_t> pc(total);
+        if (cudaMemcpyAsync(d_it.p, heavy.data(), sizeof(uint32_t) * heavy.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(d_pre.p, qpre.data(), sizeof(uint64_t) * qpre.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return unreserve(cuda_fail(cudaGetLastError(), "heavy item list"));
+        k_pair_cost<<<grid_for(total, 256, 8192), 256, 0, st>>>(G->gd, G->items.as<Item>(), d_it.as<uint32_t>(),
+                                                               d_pre.as<uint64_t>(), (uint32_t)heavy.size(), total,
+                                                               (int)s->opts.algo, s->opts.chunk,
+                                                               d_pc.as<unsigned long long>());
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(pc.data(), d_pc.p, sizeof(uint64_t) * total, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return unreserve(cuda_fail(cudaGetLastError(), "pair costs of heavy items"));
+        std::vector<Item> nitems;
+        std::vector<uint64_t> ncost;
+        nitems.reserve(G->n_items + total / 4);
+        size_t q = 0;
+        for (uint32_t i = 0; i < G->n_items; ++i) {
+            if (q < heavy.size() && heavy[q] == i) {
+                const Item w = hitems[i];
+                uint64_t pair_sum = 0;
+                for (uint64_t p = qpre[q]; p < qpre[q + 1]; ++p) pair_sum += pc[p];
+                const uint64_t stage = hi[i] > pair_sum ? hi[i] - pair_sum : 0;   // deg(u)
+                const uint64_t cap = std::max<uint64_t>(s->max_item_units, 4 * stage);
+                uint32_t start = w.j0;
+                uint64_t acc = stage;
+                for (uint32_t j = w.j0; j < w.j1; ++j) {
+                    const uint64_t c = pc[qpre[q] + (j - w.j0)];
+                    if (j > start && acc + c > cap) {
+                        nitems.push_back(Item{w.u, start, j, 0});
+                        ncost.push_back(acc);
+                        start = j;
+                        acc = stage;
+                    }
+                    acc += c;
+                }
+                nitems.push_back(Item{w.u, start, w.j1, 0});
+                ncost.push_back(acc);
+                ++q;
+            } else {
+                nitems.push_back(hitems[i]);
+                ncost.push_back(hi[i]);
+            }
+        }
+        if (nitems.size() != G->n_items) {
+            const uint64_t add = sizeof(Item) * (nitems.size() - G->n_items);
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                if (s->resident + add > s->budget) {
+                    s->n_refused++;
+                    s->resident -= G->bytes;
+                    return fail(TC_ERR_OOM, "admission refused: the split work plan exceeds the budget");
+                }
+                s->resident += add;
+                G->bytes += add;
+            }
+            if (G->items.alloc_persistent(sizeof(Item) * nitems.size()) != TC_OK ||
+                cudaMemcpyAsync(G->items.p, nitems.data(), sizeof(Item) * nitems.size(), cudaMemcpyHostToDevice, st) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return unreserve(cuda_fail(cudaGetLastError(), "split work plan"));
+            G->n_items = (uint32_t)nitems.size();
+            hi.swap(ncost);
+        }
+    }
     G->item_pre.assign(G->n_items + 1, 0);
     G->block_pre.assign(G->n_blocks + 1, 0);
     for (uint32_t i = 0; i < G->n_items; ++i) G->item_pre[i + 1] = G->item_pre[i] + std::max<uint64_t>(hi[i], 1);

@@ -104,6 +104,20 @@ def test_lane_and_quantum_settings_keep_counts(tc, pool, lanes, quantum):
         assert r.lane < lanes
 
 
+def test_split_work_items_keep_counts(tc, pool):
+    """A tiny item cap cuts every hub item into many pair ranges (each restaging N[u])."""
+    gs, want, _ = pool
+    order = list(range(len(gs))) * 2
+    res, rid_graph, ids, _ = _serve(tc, gs, order, {"quantum_us": 200, "max_item_units": 1})
+    for r in res:
+        assert r.census() == want[rid_graph[r.id]]
+    with tc.Server({"max_item_units": 1}, SUFFIX) as srv, tc.Server(None, SUFFIX) as ref:
+        gid, rid = srv.add(gs[6]), ref.add(gs[6])             # R-MAT scale 16
+        split_items = tc.tc_server_graph_units(srv.handle, gid)[1]
+        plain_items = tc.tc_server_graph_units(ref.handle, rid)[1]
+        assert split_items > plain_items
+
+
 def test_union_kernel_server(tc, pool):
     gs, want, _ = pool
     order = list(range(len(gs))) * 2
