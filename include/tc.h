@@ -341,6 +341,31 @@ tc_status tc_server_graph_units(tc_server* s, uint32_t graph_id, uint64_t* units
  * then free the server (registered graphs are not destroyed). */
 void tc_server_destroy(tc_server* s);
 
+/* ------------------------------------------------------------------ interval census
+ * The census of a network observed as a stream of timestamped arcs, taken at chosen times over
+ * a sliding window (the paper's monitoring application, Sec. 3: the census at fixed intervals).
+ * The census at time t covers the arcs with t - window < time <= t, as a set (self-loops and
+ * repeated arcs dropped) on the n vertices; it is exactly tc_census of those arcs.  The arcs of
+ * the window stay on the device; each census builds that window's graph there and counts it.
+ * Not thread-safe: one caller at a time per stream. */
+typedef struct tc_stream tc_stream;
+/* window > 0 in the caller's time unit; opt (may be NULL) as for tc_graph_create_arcs and
+ * tc_census; `stream` is the CUDA stream every copy, build and census of this object uses. */
+tc_status tc_stream_create(uint32_t n, uint64_t window, const tc_options* opt, void* stream, tc_stream** out);
+/* Append m arcs src[i] -> dst[i] at times t[i] (host arrays, copied before return).  Times must
+ * not decrease, within the call and across calls (TC_ERR_ARG); ids >= n give TC_ERR_RANGE;
+ * on error nothing is appended. */
+tc_status tc_stream_push(tc_stream* s, uint64_t m, const uint32_t* src, const uint32_t* dst, const uint64_t* t);
+/* Census of the window ending at t_now (Fig. 5, out as for tc_census); *arcs_in_window (may be
+ * NULL) receives the number of arcs pushed into the window, before loops and repeats are
+ * dropped.  t_now must not decrease across calls (TC_ERR_ARG): arcs older than the window are
+ * freed after each census.  Synchronises the stream. */
+tc_status tc_stream_census(tc_stream* s, uint64_t t_now, tc_u128 out[16], uint64_t* arcs_in_window);
+/* Arcs held (pushed and not yet older than the last census's window), device capacity in
+ * arcs, and censuses taken; any pointer may be NULL. */
+tc_status tc_stream_stats(const tc_stream* s, uint64_t* live_arcs, uint64_t* capacity, uint64_t* censuses);
+void tc_stream_destroy(tc_stream* s);
+
 /* The 64-entry tricode -> class table the kernels use (for inspection and tests). */
 void tc_tricode_table(uint8_t out[64]);
 

@@ -149,6 +149,11 @@ SIGNATURES = {
                                              ctypes.POINTER(_U32)]),
     "tc_server_trace": (ctypes.c_int, [_VP, ctypes.POINTER(tc_wave_record), _U32, ctypes.POINTER(_U32)]),
     "tc_server_destroy": (None, [_VP]),
+    "tc_stream_create": (ctypes.c_int, [_U32, _U64, _VP, _VP, ctypes.POINTER(_VP)]),
+    "tc_stream_push": (ctypes.c_int, [_VP, _U64, _VP, _VP, _VP]),
+    "tc_stream_census": (ctypes.c_int, [_VP, _U64, ctypes.POINTER(tc_u128), ctypes.POINTER(_U64)]),
+    "tc_stream_stats": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
+    "tc_stream_destroy": (None, [_VP]),
     "tc_tricode_table": (None, [ctypes.POINTER(ctypes.c_uint8)]),
 }
 
@@ -607,6 +612,55 @@ class Server:
         try:
             if self.handle:
                 self.close()
+        except Exception:
+            pass
+
+
+class Stream:
+    """Interval census over a stream of timestamped arcs (owning wrapper around tc_stream)."""
+
+    def __init__(self, n: int, window: int, options=None, stream=None):
+        po, self._keep = _options(options)
+        out = _VP()
+        _check(load().tc_stream_create(n, window, po, _stream_handle(stream), ctypes.byref(out)), "tc_stream_create")
+        self.handle, self.n = out.value, n
+
+    def push(self, src, dst, t) -> None:
+        s = np.ascontiguousarray(src, dtype=np.uint32)
+        d = np.ascontiguousarray(dst, dtype=np.uint32)
+        tt = np.ascontiguousarray(t, dtype=np.uint64)
+        if not (len(s) == len(d) == len(tt)):
+            raise ValueError("src, dst and t must have the same length")
+        _check(load().tc_stream_push(self.handle, len(s), s.ctypes.data, d.ctypes.data, tt.ctypes.data),
+               "tc_stream_push")
+
+    def census(self, t_now: int):
+        """(16 counts, arcs pushed into the window) for the window ending at t_now."""
+        out = (tc_u128 * 16)()
+        m = _U64()
+        _check(load().tc_stream_census(self.handle, t_now, out, ctypes.byref(m)), "tc_stream_census")
+        return [out[i].value() for i in range(16)], int(m.value)
+
+    def stats(self) -> dict:
+        a, b, c = _U64(), _U64(), _U64()
+        _check(load().tc_stream_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "tc_stream_stats")
+        return {"live_arcs": int(a.value), "capacity": int(b.value), "censuses": int(c.value)}
+
+    def close(self):
+        if self.handle:
+            load().tc_stream_destroy(self.handle)
+        self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
 

@@ -112,3 +112,19 @@ def test_struct_layouts_match_header(lib, tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(st), name
         for f, _ in st._fields_:
             assert got[(name, f)] == getattr(st, f).offset, (name, f)
+
+
+def test_stream_arguments_are_checked_without_a_gpu(lib):
+    import paper_1209_6308_gb300 as tc
+    out = ctypes.c_void_p()
+    assert lib.tc_stream_create((1 << 30) + 1, 10, None, None, ctypes.byref(out)) == tc.TC_ERR_RANGE
+    assert lib.tc_stream_create(10, 0, None, None, ctypes.byref(out)) == tc.TC_ERR_ARG
+    assert lib.tc_stream_create(10, 5, None, None, ctypes.byref(out)) == tc.TC_OK
+    s = np.array([1, 2], np.uint32)
+    d = np.array([2, 3], np.uint32)
+    t = np.array([5, 4], np.uint64)                            # decreasing
+    assert lib.tc_stream_push(out, 2, s.ctypes.data, d.ctypes.data, t.ctypes.data) == tc.TC_ERR_ARG
+    bad = np.array([1, 99], np.uint32)                         # id >= n
+    t2 = np.array([4, 5], np.uint64)
+    assert lib.tc_stream_push(out, 2, bad.ctypes.data, d.ctypes.data, t2.ctypes.data) == tc.TC_ERR_RANGE
+    lib.tc_stream_destroy(out)
