@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--autotune-trials", type=int, default=12)
     p.add_argument("--no-learned", action="store_true", help="skip the learned-schedule comparison")
     p.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) run")
+    p.add_argument("--no-interval", action="store_true", help="skip the interval (windowed stream) census run")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="measured seconds per serving arm")
     p.add_argument("--serve-warmup", type=float, default=5.0, help="unmeasured seconds before them")
     p.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
@@ -420,6 +421,33 @@ def serving_comparison(tc, torch, sh, model, args):
     return out
 
 
+def interval_comparison(tc, torch, s, d, n, sh):
+    """Interval census (the paper's monitoring use): the bench graph's arcs in a random order at
+    uniform times over [0, 1000), a window of 200, a census every 100 from 200 to 1000; each
+    census builds the window's graph on the device and counts it (about a fifth of the arcs)."""
+    import numpy as np
+    rng = np.random.default_rng(7)
+    perm = rng.permutation(len(s))
+    t = np.sort(rng.integers(0, 1000, len(s))).astype(np.uint64)
+    src, dst = s[perm], d[perm]
+    times, windows = [], []
+    with tc.Stream(n, 200, options={"algo": tc.TC_ALGO_SUFFIX}, stream=sh) as st:
+        t0 = time.perf_counter()
+        st.push(src, dst, t)
+        push_s = time.perf_counter() - t0
+        for t_now in range(200, 1001, 100):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, m = st.census(t_now)
+            times.append((time.perf_counter() - t1) * 1e3)
+            windows.append(m)
+    ms = statistics.median(times)
+    return {"workload": WORKLOAD["name"] + "_times_uniform1000_window200_every100", "censuses": len(times),
+            "arcs_per_window_median": int(statistics.median(windows)), "ms_per_census_median": ms,
+            "arcs_per_s": statistics.median(windows) / (ms * 1e-3), "push_s": push_s,
+            "note": "per census: window graph build (sort, dedupe, relabel, CSR, tables) + census + D2H of 16 counts"}
+
+
 def run_gpu(args):
     import torch
     import paper_1209_6308_gb300 as tc
@@ -507,6 +535,10 @@ def run_gpu(args):
         if dist:
             dist.destroy_process_group()
         return 0
+    interval_line = None
+    if not args.no_interval:
+        log("interval census")
+        interval_line = interval_comparison(tc, torch, s, d, n, sh)
     serve_line = None
     if not args.no_serve:
         log("serving")
@@ -542,6 +574,8 @@ def run_gpu(args):
     }
     if learned_line is not None:
         line["learned"] = learned_line
+    if interval_line is not None:
+        line["interval"] = interval_line
     if serve_line is not None:
         line["serving"] = serve_line
     if not args.no_batch:
