@@ -47,6 +47,12 @@ constexpr uint32_t kEmpty = 0u;              // stored entries always have dir !
 constexpr int kUnroll = TC_UNROLL;           // v-side entries in flight per lane (per trip)
 constexpr uint32_t kTrip = 32u * TC_UNROLL;  // entries of N[v] per warp trip
 
+// Membership of the staged chunk of N[u]: ids below kMapIds (the highest-degree vertices, which
+// make up most of the N[v] entries walked) sit in a direct map of two direction bits per id;
+// the rest in the open-addressing hash.
+template <int ALGO> constexpr uint32_t map_ids() { return ALGO == TC_ALGO_UNION ? (1u << 16) : (1u << 17); }
+constexpr uint32_t kHashFactorUnion = 2, kHashFactorSuffix = 2;
+
 __device__ uint8_t d_tricode_class[64];
 
 struct Params {
@@ -201,15 +207,23 @@ __device__ __forceinline__ void load_trip(uint32_t (&x)[kUnroll], const uint32_t
 // VT: every entry walked is past u; a common neighbour is counted by dir(v,w) (the v-only
 // triads come from the pair's suffix counts), and one past v also credits the pair (v, w)
 // with the common neighbour u, in the dyadic class of dir(v,w).
-template <bool VT>
-__device__ __forceinline__ void classify_trip(const uint32_t (&cur)[kUnroll], const uint32_t* sH, int hb,
-                                              uint32_t hmask, uint32_t u, uint32_t v, uint32_t cuv,
-                                              const uint8_t* sT, Counts& k, PairAcc& pa) {
+template <bool VT, uint32_t MAPIDS>
+__device__ __forceinline__ void classify_trip(const uint32_t (&cur)[kUnroll], const uint32_t* sH,
+                                              const uint32_t* sMap, int hb, uint32_t hmask, uint32_t u, uint32_t v,
+                                              uint32_t cuv, const uint8_t* sT, Counts& k, PairAcc& pa) {
     uint32_t h[kUnroll], e[kUnroll];
 #pragma unroll
     for (int r = 0; r < kUnroll; ++r) {
-        h[r] = hash_slot(cur[r] >> 2, hb);
-        e[r] = cur[r] ? sH[h[r]] : kEmpty;
+        const uint32_t x = cur[r] >> 2;
+        h[r] = hash_slot(x, hb);
+        if (!cur[r]) {
+            e[r] = kEmpty;
+        } else if (x < MAPIDS) {   // direct map: the entry's direction bits, 0 if absent
+            const uint32_t dir = (sMap[x >> 4] >> ((x & 15u) << 1)) & 3u;
+            e[r] = dir ? ((cur[r] & ~3u) | dir) : kEmpty;
+        } else {
+            e[r] = sH[h[r]];
+        }
     }
 #pragma unroll
     for (int r = 0; r < kUnroll; ++r) {
@@ -249,9 +263,10 @@ __device__ __forceinline__ void classify_trip(const uint32_t (&cur)[kUnroll], co
 // The v side of one pair (u, v) in a chunked hub: every w of N[v] from position k0 up to the
 // chunk's id bound is looked up in the staged hash of N[u].  Returns the position after the
 // last entry taken.
-template <bool VT>
+template <bool VT, uint32_t MAPIDS>
 __device__ __forceinline__ uint32_t v_side_chunk(const uint32_t* __restrict__ B, uint32_t k0, uint32_t dv,
-                                                 uint32_t hi_key, const uint32_t* sH, int hb, uint32_t hmask,
+                                                 uint32_t hi_key, const uint32_t* sH, const uint32_t* sMap, int hb,
+                                                 uint32_t hmask,
                                                  uint32_t u, uint32_t v, uint32_t duv, uint32_t cuv, const uint8_t* sT,
                                                  Counts& k, PairAcc& pa, int lane) {
     uint32_t cur[kUnroll], nxt[kUnroll];
@@ -260,7 +275,7 @@ __device__ __forceinline__ uint32_t v_side_chunk(const uint32_t* __restrict__ B,
         pk_maybe_flush(k, lane);
         if (pa.trips >= kPairSpillTrips) pair_fold<VT>(k, pa, lane, duv, cuv, sT, 0ull, 0ull);
         load_trip<true>(nxt, B, k0 + kTrip, dv, hi_key, lane);
-        classify_trip<VT>(cur, sH, hb, hmask, u, v, cuv, sT, k, pa);
+        classify_trip<VT, MAPIDS>(cur, sH, sMap, hb, hmask, u, v, cuv, sT, k, pa);
         uint32_t taken = 0;
 #pragma unroll
         for (int r = 0; r < kUnroll; ++r) taken += __popc(__ballot_sync(0xffffffffu, cur[r] != 0u));
@@ -285,12 +300,14 @@ template <int ALGO, int MODE, bool VT>
 __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t chunk = P.chunk;
-    constexpr uint32_t kHashFactor = ALGO == TC_ALGO_UNION ? 2u : 4u;
+    constexpr uint32_t kHashFactor = ALGO == TC_ALGO_UNION ? kHashFactorUnion : kHashFactorSuffix;
+    constexpr uint32_t kMap = map_ids<ALGO>();
     // TC_ALGO_UNION keeps the sorted chunk for its walk; the suffix form needs the hash, the
     // direction bit planes and their block prefix counts
     uint32_t* sA = reinterpret_cast<uint32_t*>(smem);                                  // [chunk] (union)
     uint32_t* sH = sA + (ALGO == TC_ALGO_UNION ? chunk : 0u);                          // [kHashFactor*chunk]
-    uint32_t* sLo = sH + kHashFactor * chunk;                                          // [chunk/32] dir bit 0
+    uint32_t* sMap = sH + kHashFactor * chunk;                                         // [kMap/16]
+    uint32_t* sLo = sMap + kMap / 16;                                                  // [chunk/32] dir bit 0
     uint32_t* sHi = sLo + chunk / 32;                                                  // [chunk/32] dir bit 1
     unsigned long long* sCk = reinterpret_cast<unsigned long long*>(sHi + chunk / 32); // [chunk/32+1]
     uint32_t* sCur = reinterpret_cast<uint32_t*>(sCk + chunk / 32 + 1);               // [kMaxItemPairs]
@@ -371,6 +388,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
             while ((1u << hb) < kHashFactor * LA) ++hb;
             const uint32_t H = 1u << hb, hmask = H - 1;
             for (uint32_t k = tid; k < H; k += kThreads) sH[k] = kEmpty;
+            for (uint32_t k = tid; k < kMap / 16; k += kThreads) sMap[k] = 0u;
             if (tid == 0) s_next = 0;
             __syncthreads();
             // stage the chunk: hash (both forms), sorted copy (union), direction bit planes (suffix)
@@ -380,8 +398,13 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                 const uint32_t e = idx < LA ? Ach[idx] : 0u;
                 if (idx < LA) {
                     if (ALGO == TC_ALGO_UNION) sA[idx] = e;
-                    uint32_t h = hash_slot(e >> 2, hb);
-                    while (atomicCAS(&sH[h], kEmpty, e) != kEmpty) h = (h + 1) & hmask;
+                    const uint32_t x = e >> 2;
+                    if (x < kMap) {
+                        atomicOr(&sMap[x >> 4], (e & 3u) << ((x & 15u) << 1));
+                    } else {
+                        uint32_t h = hash_slot(x, hb);
+                        while (atomicCAS(&sH[h], kEmpty, e) != kEmpty) h = (h + 1) & hmask;
+                    }
                 }
                 if (ALGO == TC_ALGO_SUFFIX) {
                     const uint32_t bl = __ballot_sync(0xffffffffu, e & 1u), bh = __ballot_sync(0xffffffffu, e & 2u);
@@ -468,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                         const uint32_t dv = __shfl_sync(0xffffffffu, dv_l, t);
                         const uint32_t start = __shfl_sync(0xffffffffu, cur_l, t);
                         const uint32_t v = euv >> 2, duv = euv & 3u, cuv = code_uv(duv);
-                        const uint32_t kend = v_side_chunk<VT>(adj + vb, start, dv, hi_key, sH, hb, hmask, u, v, duv, cuv,
+                        const uint32_t kend = v_side_chunk<VT, kMap>(adj + vb, start, dv, hi_key, sH, sMap, hb, hmask, u, v, duv, cuv,
                                                                sT, cnt, pa, lane);
                         if (lane == 0) sCur[base + t] = kend;
                         finish_pair(t, duv, cuv, dv);
@@ -506,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                             ndv = __shfl_sync(0xffffffffu, dv_l, nt);
                         }
                         if (more) load_trip<false>(nxt, adj + nvb, nk0, ndv, 0u, lane);
-                        classify_trip<VT>(cur, sH, hb, hmask, u, v, cuv, sT, cnt, pa);
+                        classify_trip<VT, kMap>(cur, sH, sMap, hb, hmask, u, v, cuv, sT, cnt, pa);
                         if (nt != t) {
                             if (nchunks > 1 && lane == 0) sCur[base + t] = dv;
                             finish_pair(t, duv, cuv, dv);
@@ -711,9 +734,11 @@ std::atomic<uint64_t> g_attr_set[2 * kForms] = {};
 std::atomic<int> g_dyn_limit[2 * kForms] = {};   // per kernel form: optin - static smem
 
 size_t census_smem(uint32_t algo, uint32_t chunk) {
-    return sizeof(uint32_t) * (algo == TC_ALGO_UNION ? 3ull : 4ull) * chunk + sizeof(uint32_t) * (chunk / 16) +
-           sizeof(unsigned long long) * (chunk / 32 + 1) + sizeof(uint32_t) * kMaxItemPairs +
-           sizeof(unsigned long long) * 16 + 64;
+    const bool uni = algo == TC_ALGO_UNION;
+    const unsigned long long words = (uni ? 1ull + kHashFactorUnion : (unsigned long long)kHashFactorSuffix) * chunk +
+                                     (uni ? map_ids<TC_ALGO_UNION>() : map_ids<TC_ALGO_SUFFIX>()) / 16;
+    return sizeof(uint32_t) * words + sizeof(uint32_t) * (chunk / 16) + sizeof(unsigned long long) * (chunk / 32 + 1) +
+           sizeof(uint32_t) * kMaxItemPairs + sizeof(unsigned long long) * 16 + 64;
 }
 
 tc_status prepare_device(cudaStream_t st, int algo, size_t smem) {
