@@ -89,8 +89,8 @@ typedef struct {
     uint64_t sum_walk;        /* sum over upper pairs u<v of |{w in N(v): w > u}|: the N[v] entries
                                  a census walks */
 } tc_graph_info;
-/* bytes_alg = 16(n+1) + 36 e_sym + 4 sum_walk + 128: the CSR read once (offsets 8(n+1), lists
- * 8 e_sym), the per-pair tables (8(n+1) + 12 e_sym), 16 B of bookkeeping per pair, 4 B per
+/* bytes_alg = 16(n+1) + 44 e_sym + 4 sum_walk + 128: the CSR read once (offsets 8(n+1), lists
+ * 8 e_sym), the per-pair tables (8(n+1) + 20 e_sym), 16 B of bookkeeping per pair, 4 B per
  * N[v] entry walked, and the 16 counters. */
 
 /* Build a graph from an arc list (Sec. 6, Fig. 7).  src[i] -> dst[i] for i < m; self-loops

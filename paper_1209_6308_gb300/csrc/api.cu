@@ -259,7 +259,7 @@ tc_status tc_graph_stats(const tc_graph* g, tc_graph_info* info) {
     info->sum_d2 = s.sum_d2;
     info->sum_dv_upper = s.sum_dv_upper;
     info->sum_walk = s.sum_walk;
-    info->bytes_alg = 16ull * (s.n + 1ull) + 36ull * s.e_sym + 4ull * s.sum_walk + 128ull;
+    info->bytes_alg = 16ull * (s.n + 1ull) + 44ull * s.e_sym + 4ull * s.sum_walk + 128ull;
     return TC_OK;
 }
 

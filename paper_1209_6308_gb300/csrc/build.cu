@@ -155,14 +155,16 @@ __global__ void k_graph_sums(const uint64_t* off, const uint32_t* adj, const uin
 
 // Per upper pair tables.  One warp per vertex v takes N[v] in 32-entry blocks from the end,
 // keeping running counts of the direction classes of the entries behind the block and adding,
-// per lane, the block's entries after its own by ballot: so the lane at a lower neighbour
-// u = N[v][k] (k < up[v]) knows the counts of the entries after k, i.e. of the third vertices
-// w > u reached from v.  It finds the upper pair (u, v) in N[u] by binary search and writes
-// rp = k and vs = (class-1, class-2 counts).  wk[0] += the suffix lengths (the N[v] entries a
-// census walks).
+// per lane, the block's entries after its own by ballot: so the lane at position k knows the
+// counts of the entries after k.  At a lower neighbour u = N[v][k] (k < up[v]) those are the
+// third vertices w > u reached from v: the lane finds the upper pair (u, v) in N[u] by binary
+// search and writes rp = k and vs = (class-1, class-2 counts).  At an upper neighbour
+// (k >= up[v]) they are the third vertices w > N[v][k] reached from v, the u side of the pair
+// (v, N[v][k]): us = (class-1, class-2 counts).  wk[0] += the suffix lengths at lower
+// neighbours (the N[v] entries a census walks).
 __global__ void k_pair_tables(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
                               const uint32_t* __restrict__ up, const uint64_t* __restrict__ ub, uint32_t n,
-                              uint32_t* rp, uint2* vs, unsigned long long* wk) {
+                              uint32_t* rp, uint2* vs, uint2* us, unsigned long long* wk) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t after = lane == 31 ? 0u : ~((2u << lane) - 1u);   // lanes above this one
@@ -187,6 +189,8 @@ __global__ void k_pair_tables(const uint64_t* __restrict__ off, const uint32_t* 
                 rp[idx] = k;
                 vs[idx] = make_uint2(c1 + __popc(b1 & after), c2 + __popc(b2 & after));
                 walk += dv - k - 1;
+            } else if (k < dv) {
+                us[ub[v] + (k - lv)] = make_uint2(c1 + __popc(b1 & after), c2 + __popc(b2 & after));
             }
             c1 += __popc(b1);
             c2 += __popc(b2);
@@ -320,6 +324,7 @@ tc_status finish_graph(GraphStore& g, uint64_t E, int B, uint64_t* ukey, uint32_
         TC_TRY(g.ub.alloc_persistent(sizeof(uint64_t) * (n + 1ull)));
         TC_TRY(g.rp.alloc_persistent(sizeof(uint32_t) * (E ? E : 1)));
         TC_TRY(g.vs.alloc_persistent(sizeof(uint2) * (E ? E : 1)));
+        TC_TRY(g.us.alloc_persistent(sizeof(uint2) * (E ? E : 1)));
         if (n) {
             k_upper_of<<<gridN, kB, 0, st>>>(g.off.as<uint64_t>(), g.up.as<uint32_t>(), n, ucnt.as<uint32_t>());
             TC_LAUNCH("k_upper_of");
@@ -330,7 +335,7 @@ tc_status finish_graph(GraphStore& g, uint64_t E, int B, uint64_t* ukey, uint32_
             // such ids stops before this point
             k_pair_tables<<<grid_for((uint64_t)n * 32, kB, 1u << 16), kB, 0, st>>>(
                 g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(),
-                                                g.ub.as<uint64_t>(), n, g.rp.as<uint32_t>(), g.vs.as<uint2>(),
+                                                g.ub.as<uint64_t>(), n, g.rp.as<uint32_t>(), g.vs.as<uint2>(), g.us.as<uint2>(),
                                                 stats.as<unsigned long long>() + 1);
             TC_LAUNCH("k_pair_tables");
         }

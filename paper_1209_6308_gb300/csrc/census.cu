@@ -162,10 +162,12 @@ __device__ __forceinline__ void pk_maybe_flush(Counts& k, int lane) {
 // except in the pair's first fold), so the v-only triads are the suffix counts minus vo (mod
 // 2^64 across folds); the common neighbours w < u of the pair were credited by the pairs
 // (w, u) that met this pair's triangle, so the dyadic count takes only the walked ones.
+// usv (VT): the u side the same way, (class-1, class-2 counts, length) of N[u] past v, or zero
+// (later folds, and the union walk, which counts the u side one by one).
 template <bool VT>
 __device__ __forceinline__ void pair_fold(Counts& k, PairAcc& pa, int lane, uint32_t duv, uint32_t cuv,
                                           const uint8_t* sT, unsigned long long suf, unsigned long long dy,
-                                          uint3 vsv = make_uint3(0u, 0u, 0u)) {
+                                          uint3 vsv = make_uint3(0u, 0u, 0u), uint3 usv = make_uint3(0u, 0u, 0u)) {
     uint32_t cm = VT ? 0u : __reduce_add_sync(0xffffffffu, pa.cm);
 #pragma unroll
     for (uint32_t d = 1; d <= 3; ++d) {
@@ -179,7 +181,12 @@ __device__ __forceinline__ void pair_fold(Counts& k, PairAcc& pa, int lane, uint
         } else {
             if (lane == cv) k.racc += vs;
         }
-        if (lane == cu) k.racc += ((suf >> (21 * (d - 1))) & 0x1fffffull) - (unsigned long long)fs;
+        if (VT) {
+            const uint32_t tot = d == 1 ? usv.x : d == 2 ? usv.y : usv.z - usv.x - usv.y;
+            if (lane == cu) k.racc += (unsigned long long)tot - (unsigned long long)fs;
+        } else {
+            if (lane == cu) k.racc += ((suf >> (21 * (d - 1))) & 0x1fffffull) - (unsigned long long)fs;
+        }
     }
     if (lane == (duv == 3u ? 2 : 1)) k.racc += dy + cm;
     pa.vo = pa.fo = 0;
@@ -302,6 +309,9 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     const uint32_t chunk = P.chunk;
     constexpr uint32_t kHashFactor = ALGO == TC_ALGO_UNION ? kHashFactorUnion : kHashFactorSuffix;
     constexpr uint32_t kMap = map_ids<ALGO>();
+    // map-first items (suffix form with tables): the map is staged once per item and only the
+    // entries past it are chunked; the union walk keeps per-chunk staging for its sorted copy
+    constexpr bool MF = VT && ALGO == TC_ALGO_SUFFIX;
     // TC_ALGO_UNION keeps the sorted chunk for its walk; the suffix form needs the hash, the
     // direction bit planes and their block prefix counts
     uint32_t* sA = reinterpret_cast<uint32_t*>(smem);                                  // [chunk] (union)
@@ -313,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     uint32_t* sCur = reinterpret_cast<uint32_t*>(sCk + chunk / 32 + 1);               // [kMaxItemPairs]
     unsigned long long* sC = reinterpret_cast<unsigned long long*>(sCur + kMaxItemPairs);  // [16]
     uint8_t* sT = reinterpret_cast<uint8_t*>(sC + 16);                                // [64]
-    __shared__ uint32_t s_item, s_next;
+    __shared__ uint32_t s_item, s_next, s_pl;
     __shared__ WaveReq sReq[MODE == kModeWave ? kMaxWave : 1];
     constexpr bool MULTI = MODE != kModeSingle;
 
@@ -332,6 +342,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     const uint64_t* __restrict__ ubp = P.g.ub;
     const uint32_t* __restrict__ rpp = P.g.rp;
     const uint2* __restrict__ vsp = P.g.vs;
+    const uint2* __restrict__ usp = P.g.us;
     uint32_t cur_graph = 0xffffffffu;          // batched: the graph whose totals the lanes hold
     unsigned long long* gout = P.out;
     Counts cnt;
@@ -351,6 +362,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
         ubp = G.ub;
         rpp = G.rp;
         vsp = G.vs;
+        usp = G.us;
         gout = MODE == kModeWave ? sReq[gi].out : P.out + 16ull * gi;
     };
 
@@ -373,7 +385,27 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
         const uint32_t u = w.u;
         const uint64_t ubase = off[u];
         const uint32_t du = (uint32_t)(off[u + 1] - ubase);
-        const uint32_t nchunks = (du + chunk - 1) / chunk;
+        // MF: the map holds every entry of N[u] with an id below kMap - a prefix of the
+        // ascending list, staged once per item - and only the entries past it are chunked
+        // into the hash, so a hub mostly made of high-degree neighbours needs few chunks
+        uint32_t pL = 0;
+        if (MF) {
+            for (uint32_t k = tid; k < kMap / 16; k += kThreads) sMap[k] = 0u;
+            if (tid == 0) s_pl = 0;
+            __syncthreads();
+            for (uint32_t q = warp; q * 32u < du; q += kWarps) {
+                const uint32_t idx = q * 32u + lane;
+                const uint32_t e = idx < du ? adj[ubase + idx] : 0u, x = e >> 2;
+                const bool in = idx < du && x < kMap;
+                if (in) atomicOr(&sMap[x >> 4], (e & 3u) << ((x & 15u) << 1));
+                const uint32_t bm = __ballot_sync(0xffffffffu, in);
+                if (lane == 0 && bm) atomicAdd(&s_pl, (uint32_t)__popc(bm));
+                if (bm != 0xffffffffu) break;   // later rows hold only ids >= kMap
+            }
+            __syncthreads();
+            pL = s_pl;
+        }
+        const uint32_t nchunks = MF ? (du > pL ? (du - pL + chunk - 1) / chunk : 1u) : (du + chunk - 1) / chunk;
         const uint32_t npairs = w.j1 - w.j0;                      // <= kMaxItemPairs
         const uint32_t G = max(1u, min(32u, npairs / (4u * kWarps)));
         // table index of the item's first pair
@@ -382,13 +414,14 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
             for (uint32_t i = tid; i < npairs; i += kThreads) sCur[i] = VT ? rpp[pb + i] + 1u : 0u;
 
         for (uint32_t c = 0; c < nchunks; ++c) {
-            const uint32_t a0 = c * chunk, a1 = min(du, a0 + chunk), LA = a1 - a0;
+            const uint32_t a0 = MF ? pL + c * chunk : c * chunk, a1 = min(du, a0 + chunk), LA = a1 - a0;
             const uint32_t* __restrict__ Ach = adj + ubase + a0;
             int hb = 6;
             while ((1u << hb) < kHashFactor * LA) ++hb;
             const uint32_t H = 1u << hb, hmask = H - 1;
             for (uint32_t k = tid; k < H; k += kThreads) sH[k] = kEmpty;
-            for (uint32_t k = tid; k < kMap / 16; k += kThreads) sMap[k] = 0u;
+            if (!MF)
+                for (uint32_t k = tid; k < kMap / 16; k += kThreads) sMap[k] = 0u;
             if (tid == 0) s_next = 0;
             __syncthreads();
             // stage the chunk: hash (both forms), sorted copy (union), direction bit planes (suffix)
@@ -406,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                         while (atomicCAS(&sH[h], kEmpty, e) != kEmpty) h = (h + 1) & hmask;
                     }
                 }
-                if (ALGO == TC_ALGO_SUFFIX) {
+                if (ALGO == TC_ALGO_SUFFIX && !MF) {
                     const uint32_t bl = __ballot_sync(0xffffffffu, e & 1u), bh = __ballot_sync(0xffffffffu, e & 2u);
                     if (lane == 0) {
                         sLo[q] = bl;
@@ -416,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                 }
             }
             __syncthreads();
-            if (ALGO == TC_ALGO_SUFFIX) {
+            if (ALGO == TC_ALGO_SUFFIX && !MF) {
                 if (warp == 0) {   // inclusive scan of the block counts -> counts before each block
                     unsigned long long carry = 0;
                     for (uint32_t b = 0; b < nq; b += 32) {
@@ -451,10 +484,11 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                 const uint32_t cur_l = (okl && nchunks > 1) ? sCur[base + lane] : 0u;
                 // tables of the grabbed pairs, needed for their first chunk
                 uint32_t rp_l = 0;
-                uint2 vs_l = make_uint2(0u, 0u);
+                uint2 vs_l = make_uint2(0u, 0u), us_l = make_uint2(0u, 0u);
                 if (VT && c == 0 && okl) {
                     rp_l = rpp[pb + base + lane];
                     vs_l = vsp[pb + base + lane];
+                    if (MF) us_l = usp[pb + base + lane];
                 }
                 // u side of pair t of this grab and the fold of its counts
                 auto finish_pair = [&](uint32_t t, uint32_t duv, uint32_t cuv, uint32_t dv) {
@@ -462,7 +496,13 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                     uint32_t s0 = (j + 1 > a0 ? j + 1 : a0) - a0;        // chunk entries past v
                     if (s0 > LA) s0 = LA;
                     unsigned long long suf = 0;
-                    if (ALGO == TC_ALGO_UNION) {
+                    uint3 usv = make_uint3(0u, 0u, 0u);
+                    if (MF) {
+                        // the whole u side in the pair's first fold, from the table
+                        if (c == 0)
+                            usv = make_uint3(__shfl_sync(0xffffffffu, us_l.x, t), __shfl_sync(0xffffffffu, us_l.y, t),
+                                             du - 1u - j);
+                    } else if (ALGO == TC_ALGO_UNION) {
                         for (uint32_t kb = s0; kb < LA; kb += 32) {
                             pk_maybe_flush(cnt, lane);
                             const uint32_t k = kb + lane;
@@ -481,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                         vsv.y = __shfl_sync(0xffffffffu, vs_l.y, t);
                         vsv.z = dv - 1u - __shfl_sync(0xffffffffu, rp_l, t);
                     }
-                    pair_fold<VT>(cnt, pa, lane, duv, cuv, sT, suf, c == 0 ? n - du - dv : 0ull, vsv);
+                    pair_fold<VT>(cnt, pa, lane, duv, cuv, sT, suf, c == 0 ? n - du - dv : 0ull, vsv, usv);
                 };
                 if (has_hi) {
                     // chunked hub: each pair resumes at its cursor and stops at the chunk's id bound
@@ -659,7 +699,13 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                             suf += ballot3((k > j && k < du) ? (wA[k] & 3u) : 0u);
                         }
                     }
-                    pair_fold<VT>(cnt, pa, lane, duv, cuv, sT, suf, n - du - dv, vsv);
+                    uint3 usv = make_uint3(0u, 0u, 0u);
+                    if (VT && ALGO == TC_ALGO_SUFFIX) {   // deg(u) <= 64: the packed counts are exact
+                        const uint32_t s1 = (uint32_t)(suf & 0x1fffffull), s2 = (uint32_t)((suf >> 21) & 0x1fffffull),
+                                       s3 = (uint32_t)((suf >> 42) & 0x1fffffull);
+                        usv = make_uint3(s1, s2, s1 + s2 + s3);
+                    }
+                    pair_fold<VT>(cnt, pa, lane, duv, cuv, sT, suf, n - du - dv, vsv, usv);
                 }
             }
             if (!MULTI && P.vcost && lane == 0) P.vcost[u] += (unsigned long long)(clock64() - t_vert);

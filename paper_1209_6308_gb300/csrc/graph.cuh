@@ -43,7 +43,7 @@ struct GraphStore {
     uint32_t n = 0, n_active = 0, max_deg = 0;
     uint64_t arcs = 0, e_sym = 0, mutual = 0, loops = 0, dups = 0, sum_d2 = 0, sum_dv_upper = 0, sum_walk = 0;
     DevBuf off, adj, up, new_of_old;
-    DevBuf ub, rp, vs;   // per upper pair tables (see GraphDev)
+    DevBuf ub, rp, vs, us;   // per upper pair tables (see GraphDev)
     DevBuf ctr;        // census work counters (uint32 x 4)
     DevBuf acc;        // census accumulators (uint64 x 16)
     DevBuf cost;       // optional per-vertex predicted cost (float x n) for the learned schedule
@@ -64,6 +64,7 @@ struct GraphStore {
         d.ub = ub.as<uint64_t>();
         d.rp = rp.as<uint32_t>();
         d.vs = vs.as<uint2>();
+        d.us = us.as<uint2>();
         return d;
     }
 };

@@ -162,6 +162,7 @@ extern "C" tc_status tc_census_csr_noalloc(uint32_t n, const uint64_t* d_off, co
     gd.ub = nullptr;   // no per-pair tables: the census walks whole lists
     gd.rp = nullptr;
     gd.vs = nullptr;
+    gd.us = nullptr;
     return census_launch_raw(gd, o, items, u_end ? h[kCntItems] : 0u, u_end, n_active, cnt + kCntCensus,
                              reinterpret_cast<unsigned long long*>(d_out16), st);
 }

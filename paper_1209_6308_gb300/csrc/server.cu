@@ -709,7 +709,7 @@ tc_status tc_server_add_graph(tc_server* s, tc_graph* g, void* stream, uint32_t*
     G->n_blocks = (p->warp_end - p->warp_begin + 31) / 32;
     const uint64_t item_bytes = sizeof(Item) * (uint64_t)std::max(p->n_items, 1u);
     G->bytes = g->s.off.bytes + g->s.adj.bytes + g->s.up.bytes + g->s.new_of_old.bytes + g->s.ub.bytes +
-               g->s.rp.bytes + g->s.vs.bytes + item_bytes;
+               g->s.rp.bytes + g->s.vs.bytes + g->s.us.bytes + item_bytes;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->resident + G->bytes > s->budget) {

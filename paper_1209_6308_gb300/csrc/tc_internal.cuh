@@ -58,12 +58,14 @@ struct GraphDev {
     const uint64_t* off;    // [n+1]
     const uint32_t* adj;    // [off[n]]
     const uint32_t* up;     // [n] number of neighbours with a smaller id (index of first v > u)
-    // Per upper pair tables (null when absent): the upper pair (u, N[u][j]) with j >= up[u] has
-    // index ub[u] + j - up[u]; rp[.] is the position of u in N[v], vs[.] the counts of
-    // direction classes 1 and 2 among the entries of N[v] after u (class 3: the rest).
+    // Per upper pair tables (null when absent): the upper pair (u, v = N[u][j]) with j >= up[u]
+    // has index ub[u] + j - up[u]; rp[.] is the position of u in N[v], vs[.] the counts of
+    // direction classes 1 and 2 among the entries of N[v] after u, us[.] those among the
+    // entries of N[u] after v (class 3: the rest of each suffix).
     const uint64_t* ub;     // [n+1] upper pairs before each vertex
     const uint32_t* rp;     // [E]
     const uint2* vs;        // [E]
+    const uint2* us;        // [E]
 };
 
 // One CTA work item of the census: vertex u and its pairs (u, N[u][j]) for j in [j0, j1)
