@@ -58,8 +58,9 @@ typedef enum {
 
 /* How the connected pairs (u,v) are grouped into GPU work items. */
 typedef enum {
-    TC_SCHED_PLAIN = 0,    /* degree-threshold tiers, cost estimated from degrees */
-    TC_SCHED_LEARNED = 1   /* tiers and hub splits from the learned per-vertex cost model */
+    TC_SCHED_PLAIN = 0,    /* degree-threshold tiers; a vertex's pairs split into items by their exact work
+                              (the N[v] entries walked plus per-pair overheads) */
+    TC_SCHED_LEARNED = 1   /* the same, with each vertex's item count from the learned cost model */
 } tc_schedule;
 
 /* Options; zero-initialise and set what you need (0 selects the default). */
@@ -69,7 +70,8 @@ typedef struct {
     uint32_t warp_max_deg;    /* vertices u with deg <= this run one warp per u (default 64) */
     uint32_t chunk_entries;   /* neighbour entries of u staged per CTA: power of 2 in [512, 16384],
                                  at most 8192 for TC_ALGO_SUFFIX (default 4096) */
-    uint32_t item_work;       /* target work per CTA item, in list entries touched (default 2^18) */
+    uint32_t item_work;       /* work per CTA item, in list entries walked plus pair overheads
+                                 (0 = sized to the graph: about four items per CTA, 2^14 to 2^22) */
     uint32_t ctas_per_sm;     /* persistent CTAs per SM (default 3) */
     uint32_t reserved[10];
 } tc_options;
@@ -206,8 +208,9 @@ tc_status tc_census_csr_noalloc(uint32_t n, const uint64_t* d_off, const uint32_
 
 /* ------------------------------------------------------------------ learned schedule
  * A small network predicts, per vertex u, the SM cycles its pairs (u, v > u) cost the census
- * (Fig. 5 step 2 unit); the plan then splits u's pairs into work items by that prediction
- * (schedule TC_SCHED_LEARNED) instead of by the degree estimate.  It only reorders work: counts
+ * (Fig. 5 step 2 unit); the plan then takes u's number of work items from that prediction
+ * (schedule TC_SCHED_LEARNED) instead of from the exact work total (the cuts still follow the
+ * pairs' exact work).  It only reorders work: counts
  * are the same either way.  Network: features log1p(out-degree, in-degree, degree, sum of
  * neighbour degrees) -> 32 -> 32 -> 1 (tanh), FP16 weights, FP32 accumulation, output
  * log(cycles); trained on the GPU with Adam on cycles measured by tc_census_profile. */
@@ -230,8 +233,8 @@ tc_status tc_graph_features(const tc_graph* g, void* stream, float* d_feat4);
 /* Training samples from a profiled census: every vertex split into CTA work items (degree
  * above the graph's warp-tier threshold) with d_vcost > 0 contributes its
  * features to d_x4 and log(cycles) to d_y (device, at most `capacity`, any order); *count
- * receives the number written; est_sum / cycle_sum (may be NULL) the plain schedule's estimate
- * and the measured cycles summed over those vertices (their ratio calibrates kappa). */
+ * receives the number written; est_sum / cycle_sum (may be NULL) the plain schedule's work
+ * units and the measured cycles summed over those vertices (their ratio calibrates kappa). */
 tc_status tc_costmodel_samples(const tc_graph* g, const uint64_t* d_vcost, const float* d_feat4, uint32_t capacity,
                                void* stream, float* d_x4, float* d_y, uint32_t* count, double* est_sum,
                                double* cycle_sum);

@@ -100,7 +100,7 @@ tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out) {
         return fail(TC_ERR_ARG, "chunk_entries must be a power of two in [512, 16384] (8192 for the suffix form)");
     if (o.warp_max_deg > o.chunk / 8) return fail(TC_ERR_ARG, "warp_max_deg must be <= chunk_entries / 8");
     if (o.ctas_per_sm < 1 || o.ctas_per_sm > 8) return fail(TC_ERR_ARG, "ctas_per_sm must be in [1, 8]");
-    if (o.item_work < 256) return fail(TC_ERR_ARG, "item_work must be >= 256");
+    if (o.item_work && o.item_work < 256) return fail(TC_ERR_ARG, "item_work must be 0 (sized to the graph) or >= 256");
     *out = o;
     return TC_OK;
 }

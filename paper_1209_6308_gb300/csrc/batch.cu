@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "graph.cuh"
+#include "plan.cuh"
 
 namespace tc {
 namespace {
@@ -38,53 +39,50 @@ __global__ void k_batch_wide(const GraphDev* __restrict__ gs, const uint64_t* __
     }
 }
 
-// Items per wide vertex (same sizing as the single-graph plain plan, per-graph mean degree).
+// Items of every wide vertex of every graph (plan.cuh), one warp per vertex, tagged with the
+// graph index; the same splitting as the single-graph plain plan.
+__global__ void k_batch_work(const GraphDev* __restrict__ gs, const uint64_t* __restrict__ woff, uint32_t k,
+                             uint64_t total, uint32_t chunk, int algo, unsigned long long* W, unsigned long long* sum) {
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long acc = 0;
+    for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < total; i += warps) {
+        const uint32_t g = graph_of(woff, k, i);
+        const GraphDev G = gs[g];
+        const unsigned long long w = vertex_units(G, (uint32_t)(i - woff[g]), chunk, algo);
+        acc += w;
+        if ((threadIdx.x & 31) == 0) W[i] = w;
+    }
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sum, acc);
+}
+
 __global__ void k_batch_count(const GraphDev* __restrict__ gs, const uint64_t* __restrict__ woff, uint32_t k,
                               uint64_t total, uint32_t chunk, uint32_t item_work, int algo,
-                              const float* __restrict__ dbar, uint32_t* cnt) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+                              const unsigned long long* __restrict__ W, uint32_t* cnt) {
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < total; i += warps) {
         const uint32_t g = graph_of(woff, k, i);
-        const uint64_t x = i - woff[g];
         const GraphDev G = gs[g];
-        const uint32_t du = (uint32_t)(G.off[x + 1] - G.off[x]);
-        const uint32_t P = du - G.up[x];
-        if (P == 0) { cnt[i] = 0; continue; }
-        const uint32_t C = (du + chunk - 1) / chunk;
-        double est = (double)P * ((double)dbar[g] + 16.0 + 16.0 * (double)C) +
-                     (algo == TC_ALGO_UNION ? 0.5 * (double)P * (double)du : 0.0);
-        double s = ceil(est / (double)item_work);
-        const double smin = ceil((double)P / (double)kMaxItemPairs);
-        if (s < smin) s = smin;
-        if (s < 1.0) s = 1.0;
-        if (s > (double)P) s = (double)P;
-        cnt[i] = (uint32_t)s;
+        const uint32_t c = plan_vertex(G, (uint32_t)(i - woff[g]), chunk, item_work, algo, 0.0, W[i],
+                                       [](uint32_t, uint32_t) {});
+        if ((threadIdx.x & 31) == 0) cnt[i] = c;
     }
 }
 
 __global__ void k_batch_emit(const GraphDev* __restrict__ gs, const uint64_t* __restrict__ woff, uint32_t k,
-                             uint64_t total, const uint32_t* __restrict__ pos, const uint32_t* __restrict__ cnt,
-                             Item* items) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t S = cnt[i];
-        if (!S) continue;
+                             uint64_t total, uint32_t chunk, uint32_t item_work, int algo,
+                             const unsigned long long* __restrict__ W, const uint32_t* __restrict__ pos, Item* items) {
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < total; i += warps) {
         const uint32_t g = graph_of(woff, k, i);
-        const uint32_t x = (uint32_t)(i - woff[g]);
         const GraphDev G = gs[g];
-        const uint32_t du = (uint32_t)(G.off[x + 1] - G.off[x]);
-        const uint32_t up = G.up[x], P = du - up;
-        uint32_t o = pos[i];
-        for (uint32_t s = 0; s < S; ++s) {
-            Item it;
-            it.u = x;
-            it.j0 = up + (uint32_t)((uint64_t)P * s / S);
-            it.j1 = up + (uint32_t)((uint64_t)P * (s + 1) / S);
-            it.pad = g;
-            items[o++] = it;
-        }
+        const uint32_t x = (uint32_t)(i - woff[g]);
+        Item* out = items + pos[i];
+        const uint32_t c = plan_vertex(G, x, chunk, item_work, algo, 0.0, W[i],
+                                       [&](uint32_t j, uint32_t rank) { out[rank] = Item{x, j, 0u, g}; });
+        plan_vertex_ends(out, c, (uint32_t)(G.off[x + 1] - G.off[x]));
     }
 }
 
-// launch-order outputs -> callers' order
 __global__ void k_batch_scatter(const unsigned long long* __restrict__ src, const uint32_t* __restrict__ order,
                                 uint32_t k, unsigned long long* dst) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < 16ull * k; i += (uint64_t)gridDim.x * blockDim.x)
@@ -99,7 +97,7 @@ struct BatchStore {
     std::vector<uint32_t> order;        // launch position -> caller's index
     Opts opts;
     cudaStream_t cap = nullptr;         // stream used only to capture the launch
-    DevBuf d_graphs, d_voff, d_woff, d_dbar, d_wide, d_order, items, wblocks, ctr, out;
+    DevBuf d_graphs, d_voff, d_woff, d_wide, d_order, items, wblocks, ctr, out;
     uint32_t n_items = 0, n_wblocks = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -124,16 +122,9 @@ tc_status batch_plan(BatchStore& b, cudaStream_t st) {
     if (b.graph) { cudaGraphDestroy(b.graph); b.graph = nullptr; }
     // per-graph vertex prefix and wide counts
     std::vector<uint64_t> voff(k + 1, 0);
-    std::vector<float> dbar(k);
-    for (uint32_t i = 0; i < k; ++i) {
-        const GraphStore& g = b.graphs[i]->s;
-        voff[i + 1] = voff[i] + g.n;
-        dbar[i] = g.n_active ? (float)(2.0 * (double)g.e_sym / (double)g.n_active) : 0.f;
-    }
+    for (uint32_t i = 0; i < k; ++i) voff[i + 1] = voff[i] + b.graphs[i]->s.n;
     TC_TRY(b.d_voff.alloc_persistent(sizeof(uint64_t) * (k + 1)));
     TC_CUDA(cudaMemcpyAsync(b.d_voff.p, voff.data(), sizeof(uint64_t) * (k + 1), cudaMemcpyHostToDevice, st));
-    TC_TRY(b.d_dbar.alloc_persistent(sizeof(float) * k));
-    TC_CUDA(cudaMemcpyAsync(b.d_dbar.p, dbar.data(), sizeof(float) * k, cudaMemcpyHostToDevice, st));
     TC_TRY(b.d_wide.alloc_persistent(sizeof(uint32_t) * k));
     TC_CUDA(cudaMemsetAsync(b.d_wide.p, 0, sizeof(uint32_t) * k, st));
     if (voff[k]) {
@@ -153,22 +144,32 @@ tc_status batch_plan(BatchStore& b, cudaStream_t st) {
     b.n_items = 0;
     if (total_w) {
         if (total_w >= (1ull << 32)) return fail(TC_ERR_RANGE, "batch has too many wide vertices");
-        DevBuf cnt, pos, tot;
+        DevBuf cnt, pos, tot, wv, wt;
         TC_TRY(cnt.alloc(sizeof(uint32_t) * total_w, st));
         TC_TRY(pos.alloc(sizeof(uint32_t) * total_w, st));
         TC_TRY(tot.alloc(sizeof(uint32_t), st));
-        k_batch_count<<<grid_for(total_w, 256, 1u << 16), 256, 0, st>>>(b.d_graphs.as<GraphDev>(), b.d_woff.as<uint64_t>(), k,
-                                                                       total_w, o.chunk, o.item_work, (int)o.algo,
-                                                                       b.d_dbar.as<float>(), cnt.as<uint32_t>());
+        TC_TRY(wv.alloc(sizeof(unsigned long long) * total_w, st));
+        TC_TRY(wt.alloc(sizeof(unsigned long long), st));
+        TC_CUDA(cudaMemsetAsync(wt.p, 0, sizeof(unsigned long long), st));
+        const unsigned pgrid = grid_for(total_w * 32, 256, 1u << 16);
+        k_batch_work<<<pgrid, 256, 0, st>>>(b.d_graphs.as<GraphDev>(), b.d_woff.as<uint64_t>(), k, total_w, o.chunk,
+                                            (int)o.algo, wv.as<unsigned long long>(), wt.as<unsigned long long>());
+        TC_LAUNCH("k_batch_work");
+        unsigned long long total_units = 0;
+        TC_CUDA(cudaMemcpyAsync(&total_units, wt.p, sizeof(total_units), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        const uint32_t iw = o.item_work ? o.item_work : adaptive_item_work(total_units, (unsigned)census_grid(o));
+        k_batch_count<<<pgrid, 256, 0, st>>>(b.d_graphs.as<GraphDev>(), b.d_woff.as<uint64_t>(), k, total_w, o.chunk,
+                                             iw, (int)o.algo, wv.as<unsigned long long>(), cnt.as<uint32_t>());
         TC_LAUNCH("k_batch_count");
         TC_TRY(scan_u32(cnt.as<uint32_t>(), pos.as<uint32_t>(), total_w, tot.as<uint32_t>(), st));
         TC_CUDA(cudaMemcpyAsync(&b.n_items, tot.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
         TC_TRY(b.items.alloc_persistent(sizeof(Item) * (b.n_items ? b.n_items : 1)));
         if (b.n_items) {
-            k_batch_emit<<<grid_for(total_w, 256, 1u << 16), 256, 0, st>>>(b.d_graphs.as<GraphDev>(), b.d_woff.as<uint64_t>(),
-                                                                          k, total_w, pos.as<uint32_t>(),
-                                                                          cnt.as<uint32_t>(), b.items.as<Item>());
+            k_batch_emit<<<pgrid, 256, 0, st>>>(b.d_graphs.as<GraphDev>(), b.d_woff.as<uint64_t>(), k, total_w, o.chunk,
+                                                iw, (int)o.algo, wv.as<unsigned long long>(), pos.as<uint32_t>(),
+                                                b.items.as<Item>());
             TC_LAUNCH("k_batch_emit");
         }
         TC_CUDA(cudaStreamSynchronize(st));

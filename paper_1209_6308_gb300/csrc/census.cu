@@ -31,6 +31,7 @@
 #include <cstring>
 
 #include "graph.cuh"
+#include "plan.cuh"
 
 namespace tc {
 namespace {
@@ -733,44 +734,44 @@ __global__ void k_count_gt(const uint64_t* off, uint32_t n, uint32_t thr, uint32
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
 }
 
-// Items per vertex u < u_end: S ranges of u's pairs, S from the estimated work of u's
-// pairs (degrees for the plain schedule, the cost model if given) and at most
-// kMaxItemPairs pairs per item.
-__global__ void k_plan_count(GraphDev g, uint32_t u_end, uint32_t chunk, uint32_t item_work, int algo, float dbar,
-                             const float* cost, uint32_t* cnt) {
-    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < u_end; x += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t du = (uint32_t)(g.off[x + 1] - g.off[x]);
-        const uint32_t P = du - g.up[x];
-        if (P == 0) { cnt[x] = 0; continue; }
-        const uint32_t C = (du + chunk - 1) / chunk;
-        double est;
-        if (cost) est = (double)cost[x];
-        else est = (double)P * ((double)dbar + 16.0 + 16.0 * (double)C) +
-                   (algo == TC_ALGO_UNION ? 0.5 * (double)P * (double)du : 0.0);
-        double s = ceil(est / (double)item_work);
-        const double smin = ceil((double)P / (double)kMaxItemPairs);
-        if (s < smin) s = smin;
-        if (s < 1.0) s = 1.0;
-        if (s > (double)P) s = (double)P;
-        cnt[x] = (uint32_t)s;
+// Items of the CTA-tier vertices u < u_end (plan.cuh), one warp per vertex; the learned
+// schedule fixes each vertex's item count from its predicted cost.
+__device__ __forceinline__ double learned_items(const float* cost, uint64_t x, uint32_t item_work) {
+    return cost ? fmax(1.0, ceil((double)cost[x] / (double)item_work)) : 0.0;
+}
+
+// W[x] = the work of vertex x's upper pairs; total[0] += the sum (sizes the items when the
+// options leave item_work to the graph).
+__global__ void k_plan_work(GraphDev g, uint32_t u_end, uint32_t chunk, int algo, unsigned long long* W,
+                            unsigned long long* total) {
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long sum = 0;
+    for (uint64_t x = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; x < u_end; x += warps) {
+        const unsigned long long w = vertex_units(g, (uint32_t)x, chunk, algo);
+        sum += w;
+        if ((threadIdx.x & 31) == 0) W[x] = w;
+    }
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(total, sum);
+}
+
+__global__ void k_plan_count(GraphDev g, uint32_t u_end, uint32_t chunk, uint32_t item_work, int algo,
+                             const float* cost, const unsigned long long* W, uint32_t* cnt) {
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t x = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; x < u_end; x += warps) {
+        const uint32_t c = plan_vertex(g, (uint32_t)x, chunk, item_work, algo, learned_items(cost, x, item_work), W[x],
+                                       [](uint32_t, uint32_t) {});
+        if ((threadIdx.x & 31) == 0) cnt[x] = c;
     }
 }
 
-__global__ void k_plan_emit(GraphDev g, uint32_t u_end, const uint32_t* pos, const uint32_t* cnt, Item* items) {
-    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < u_end; x += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t S = cnt[x];
-        if (!S) continue;
-        const uint32_t du = (uint32_t)(g.off[x + 1] - g.off[x]);
-        const uint32_t up = g.up[x], P = du - up;
-        uint32_t o = pos[x];
-        for (uint32_t s = 0; s < S; ++s) {
-            Item it;
-            it.u = (uint32_t)x;
-            it.j0 = up + (uint32_t)((uint64_t)P * s / S);
-            it.j1 = up + (uint32_t)((uint64_t)P * (s + 1) / S);
-            it.pad = 0;
-            items[o++] = it;
-        }
+__global__ void k_plan_emit(GraphDev g, uint32_t u_end, uint32_t chunk, uint32_t item_work, int algo,
+                            const float* cost, const unsigned long long* W, const uint32_t* pos, Item* items) {
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t x = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; x < u_end; x += warps) {
+        Item* out = items + pos[x];
+        const uint32_t c = plan_vertex(g, (uint32_t)x, chunk, item_work, algo, learned_items(cost, x, item_work), W[x],
+                                       [&](uint32_t j, uint32_t rank) { out[rank] = Item{(uint32_t)x, j, 0u, 0u}; });
+        plan_vertex_ends(out, c, (uint32_t)(g.off[x + 1] - g.off[x]));
     }
 }
 
@@ -850,22 +851,32 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out) {
     p.warp_end = g.n_active;
     p.n_items = 0;
     if (u_end) {
-        DevBuf cnt, pos, tot;
+        DevBuf cnt, pos, tot, wv, wt;
         TC_TRY(cnt.alloc(sizeof(uint32_t) * u_end, st));
         TC_TRY(pos.alloc(sizeof(uint32_t) * u_end, st));
         TC_TRY(tot.alloc(sizeof(uint32_t), st));
-        const float dbar = g.n_active ? (float)(2.0 * (double)g.e_sym / (double)g.n_active) : 0.f;
+        TC_TRY(wv.alloc(sizeof(unsigned long long) * u_end, st));
+        TC_TRY(wt.alloc(sizeof(unsigned long long), st));
+        TC_CUDA(cudaMemsetAsync(wt.p, 0, sizeof(unsigned long long), st));
         const float* cost = (o.schedule == TC_SCHED_LEARNED) ? g.cost.as<float>() : nullptr;
-        k_plan_count<<<grid_for(u_end, 256, 4096), 256, 0, st>>>(gd, u_end, o.chunk, o.item_work, (int)o.algo, dbar, cost,
-                                                                  cnt.as<uint32_t>());
+        const unsigned pgrid = grid_for((uint64_t)u_end * 32, 256, 8192);
+        k_plan_work<<<pgrid, 256, 0, st>>>(gd, u_end, o.chunk, (int)o.algo, wv.as<unsigned long long>(),
+                                           wt.as<unsigned long long>());
+        TC_LAUNCH("k_plan_work");
+        unsigned long long total_units = 0;
+        TC_CUDA(cudaMemcpyAsync(&total_units, wt.p, sizeof(total_units), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+        const uint32_t iw = o.item_work ? o.item_work : adaptive_item_work(total_units, (unsigned)census_grid(o));
+        k_plan_count<<<pgrid, 256, 0, st>>>(gd, u_end, o.chunk, iw, (int)o.algo, cost, wv.as<unsigned long long>(),
+                                            cnt.as<uint32_t>());
         TC_LAUNCH("k_plan_count");
         TC_TRY(scan_u32(cnt.as<uint32_t>(), pos.as<uint32_t>(), u_end, tot.as<uint32_t>(), st));
         TC_CUDA(cudaMemcpyAsync(&p.n_items, tot.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
         TC_TRY(p.items.alloc_persistent(sizeof(Item) * (p.n_items ? p.n_items : 1)));
         if (p.n_items) {
-            k_plan_emit<<<grid_for(u_end, 256, 4096), 256, 0, st>>>(gd, u_end, pos.as<uint32_t>(), cnt.as<uint32_t>(),
-                                                                     p.items.as<Item>());
+            k_plan_emit<<<pgrid, 256, 0, st>>>(gd, u_end, o.chunk, iw, (int)o.algo, cost, wv.as<unsigned long long>(),
+                                               pos.as<uint32_t>(), p.items.as<Item>());
             TC_LAUNCH("k_plan_emit");
         }
         TC_CUDA(cudaStreamSynchronize(st));

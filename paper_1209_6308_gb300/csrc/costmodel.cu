@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "graph.cuh"
+#include "plan.cuh"
 
 namespace tc {
 namespace {
@@ -55,24 +56,30 @@ __global__ void k_features(const uint64_t* __restrict__ off, const uint32_t* __r
 }
 
 // Training samples: vertices with measured cycles; features, log(cycles), and the plain
-// schedule's estimate of the same vertex (for the cycles -> plan-units calibration).
-__global__ void k_samples(const uint64_t* __restrict__ off, const uint32_t* __restrict__ up, uint32_t n,
-                          const float4* __restrict__ feat, const unsigned long long* __restrict__ vcost, uint32_t chunk,
-                          uint32_t warp_max, float dbar, uint32_t cap, float4* __restrict__ sx, float* __restrict__ sy,
-                          uint32_t* cnt, double* sums) {
-    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+// schedule's work units of the same vertex (for the cycles -> plan-units calibration).  One
+// warp per vertex.
+__global__ void k_samples(GraphDev g, const float4* __restrict__ feat, const unsigned long long* __restrict__ vcost,
+                          uint32_t chunk, uint32_t warp_max, int algo, uint32_t cap, float4* __restrict__ sx,
+                          float* __restrict__ sy, uint32_t* cnt, double* sums) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t x = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; x < g.n; x += warps) {
         const unsigned long long c = vcost[x];
-        const uint32_t du = (uint32_t)(off[x + 1] - off[x]);
+        const uint64_t ubase = g.off[x];
+        const uint32_t du = (uint32_t)(g.off[x + 1] - ubase), upx = g.up[x];
         if (!c || du <= warp_max) continue;   // CTA-item vertices only: what the plan splits
-        const uint32_t P = du - up[x];
-        const uint32_t C = (du + chunk - 1) / chunk;
-        const double est = (double)P * ((double)dbar + 16.0 + 16.0 * (double)C);
-        const uint32_t i = atomicAdd(cnt, 1u);
-        if (i < cap) {
-            sx[i] = feat[x];
-            sy[i] = logf((float)c);
-            atomicAdd(&sums[0], est);
-            atomicAdd(&sums[1], (double)c);
+        const uint32_t chunks = (du + chunk - 1) / chunk;
+        unsigned long long W = 0;
+        for (uint32_t j = upx + lane; j < du; j += 32) W += pair_units(g, (uint32_t)x, ubase, du, upx, j, chunks, algo);
+        for (int o = 16; o; o >>= 1) W += __shfl_xor_sync(0xffffffffu, W, o);
+        if (lane == 0) {
+            const uint32_t i = atomicAdd(cnt, 1u);
+            if (i < cap) {
+                sx[i] = feat[x];
+                sy[i] = logf((float)c);
+                atomicAdd(&sums[0], (double)W);
+                atomicAdd(&sums[1], (double)c);
+            }
         }
     }
 }
@@ -379,13 +386,11 @@ tc_status tc_costmodel_samples(const tc_graph* g, const uint64_t* d_vcost, const
     TC_TRY(sums.alloc(sizeof(double) * 2, st));
     TC_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(uint32_t), st));
     TC_CUDA(cudaMemsetAsync(sums.p, 0, sizeof(double) * 2, st));
-    const float dbar = s.n_active ? (float)(2.0 * (double)s.e_sym / (double)s.n_active) : 0.f;
     if (s.n) {
-        k_samples<<<grid_for(s.n, 256, 1u << 16), 256, 0, st>>>(
-            s.off.as<uint64_t>(), s.up.as<uint32_t>(), s.n, reinterpret_cast<const float4*>(d_feat4),
-            reinterpret_cast<const unsigned long long*>(d_vcost), o.chunk, o.warp_max_deg, dbar, capacity,
-            reinterpret_cast<float4*>(d_x4),
-            d_y, cnt.as<uint32_t>(), sums.as<double>());
+        k_samples<<<grid_for((uint64_t)s.n * 32, 256, 1u << 16), 256, 0, st>>>(
+            s.dev(), reinterpret_cast<const float4*>(d_feat4), reinterpret_cast<const unsigned long long*>(d_vcost),
+            o.chunk, o.warp_max_deg, (int)o.algo, capacity, reinterpret_cast<float4*>(d_x4), d_y, cnt.as<uint32_t>(),
+            sums.as<double>());
         TC_LAUNCH("k_samples");
     }
     uint32_t c = 0;

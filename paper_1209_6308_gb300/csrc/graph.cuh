@@ -16,7 +16,7 @@ struct Opts {
     uint32_t schedule = TC_SCHED_PLAIN;
     uint32_t warp_max_deg = 64;
     uint32_t chunk = 0;
-    uint32_t item_work = 1u << 18;
+    uint32_t item_work = 0;   // 0: sized to the graph (adaptive_item_work)
     uint32_t ctas_per_sm = 0;
     bool operator==(const Opts& o) const {
         return algo == o.algo && schedule == o.schedule && warp_max_deg == o.warp_max_deg && chunk == o.chunk &&
@@ -26,6 +26,14 @@ struct Opts {
 
 // Overlay the non-zero fields of `in` on `base`, fill the automatic values and validate.
 tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out);
+// Work units per CTA item when none is set: about four items per CTA of the launch, so a large
+// census re-stages hub lists rarely and a small one still spreads over every SM.
+inline uint32_t adaptive_item_work(unsigned long long total_units, unsigned grid) {
+    unsigned long long w = total_units / (4ull * (grid ? grid : 1u));
+    if (w < (1ull << 14)) w = 1ull << 14;
+    if (w > (1ull << 22)) w = 1ull << 22;
+    return (uint32_t)w;
+}
 // Overlay only (automatic values kept), for a graph's stored defaults.
 Opts merge_opts(const tc_options* in, const Opts* base);
 

@@ -144,7 +144,8 @@ extern "C" tc_status tc_census_csr_noalloc(uint32_t n, const uint64_t* d_off, co
     const uint32_t u_end = h[kCntWideVerts], n_active = h[kCntActive];
     const float dbar = n_active ? (float)((double)total / (double)n_active) : 0.f;
     if (u_end) {
-        k_noalloc_items<<<grid_for(u_end, 256, 4096), 256, 0, st>>>(u_end, d_off, up, o.chunk, o.item_work, dbar, cnt,
+        k_noalloc_items<<<grid_for(u_end, 256, 4096), 256, 0, st>>>(u_end, d_off, up, o.chunk,
+                                                                    o.item_work ? o.item_work : (1u << 18), dbar, cnt,
                                                                      items);
         TC_LAUNCH("k_noalloc_items");
         TC_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, st));
