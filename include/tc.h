@@ -73,7 +73,9 @@ typedef struct {
     uint32_t item_work;       /* work per CTA item, in list entries walked plus pair overheads
                                  (0 = sized to the graph: about four items per CTA, 2^14 to 2^22) */
     uint32_t ctas_per_sm;     /* persistent CTAs per SM (default 3) */
-    uint32_t reserved[10];
+    uint32_t map_mode;        /* direct id map of the staged lists in a single-graph census: 0 = when at
+                                 least half the walked lookups fall in its range, 1 = always, 2 = never */
+    uint32_t reserved[9];
 } tc_options;
 
 /* Statistics of a built graph (all counts after cleaning). */
@@ -90,6 +92,7 @@ typedef struct {
     uint64_t bytes_alg;       /* algorithmic bytes of one census (below) */
     uint64_t sum_walk;        /* sum over upper pairs u<v of |{w in N(v): w > u}|: the N[v] entries
                                  a census walks */
+    uint64_t sum_walk_map;    /* those of them with ids below 2^17 (answered by the direct id map) */
 } tc_graph_info;
 /* bytes_alg = 16(n+1) + 44 e_sym + 4 sum_walk + 128: the CSR read once (offsets 8(n+1), lists
  * 8 e_sym), the per-pair tables (8(n+1) + 20 e_sym), 16 B of bookkeeping per pair, 4 B per

@@ -41,14 +41,14 @@ class tc_u128(ctypes.Structure):
 class tc_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_uint32), ("schedule", ctypes.c_uint32), ("warp_max_deg", ctypes.c_uint32),
                 ("chunk_entries", ctypes.c_uint32), ("item_work", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 10)]
+                ("map_mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 9)]
 
 
 class tc_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("max_deg", ctypes.c_uint32), ("arcs", ctypes.c_uint64),
                 ("e_sym", ctypes.c_uint64), ("mutual", ctypes.c_uint64), ("loops_dropped", ctypes.c_uint64),
                 ("dups_dropped", ctypes.c_uint64), ("sum_d2", ctypes.c_uint64), ("sum_dv_upper", ctypes.c_uint64),
-                ("bytes_alg", ctypes.c_uint64), ("sum_walk", ctypes.c_uint64)]
+                ("bytes_alg", ctypes.c_uint64), ("sum_walk", ctypes.c_uint64), ("sum_walk_map", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

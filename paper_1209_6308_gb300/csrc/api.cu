@@ -85,6 +85,7 @@ Opts merge_opts(const tc_options* in, const Opts* base) {
         if (in->chunk_entries) o.chunk = in->chunk_entries;
         if (in->item_work) o.item_work = in->item_work;
         if (in->ctas_per_sm) o.ctas_per_sm = in->ctas_per_sm;
+        if (in->map_mode) o.map_mode = in->map_mode;
     }
     return o;
 }
@@ -100,6 +101,7 @@ tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out) {
         return fail(TC_ERR_ARG, "chunk_entries must be a power of two in [512, 16384] (8192 for the suffix form)");
     if (o.warp_max_deg > o.chunk / 8) return fail(TC_ERR_ARG, "warp_max_deg must be <= chunk_entries / 8");
     if (o.ctas_per_sm < 1 || o.ctas_per_sm > 8) return fail(TC_ERR_ARG, "ctas_per_sm must be in [1, 8]");
+    if (o.map_mode > 2) return fail(TC_ERR_ARG, "map_mode must be 0, 1 or 2");
     if (o.item_work && o.item_work < 256) return fail(TC_ERR_ARG, "item_work must be 0 (sized to the graph) or >= 256");
     *out = o;
     return TC_OK;
@@ -259,6 +261,7 @@ tc_status tc_graph_stats(const tc_graph* g, tc_graph_info* info) {
     info->sum_d2 = s.sum_d2;
     info->sum_dv_upper = s.sum_dv_upper;
     info->sum_walk = s.sum_walk;
+    info->sum_walk_map = s.sum_walk_map;
     info->bytes_alg = 16ull * (s.n + 1ull) + 44ull * s.e_sym + 4ull * s.sum_walk + 128ull;
     return TC_OK;
 }

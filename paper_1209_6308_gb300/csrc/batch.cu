@@ -62,7 +62,11 @@ __global__ void k_batch_count(const GraphDev* __restrict__ gs, const uint64_t* _
     for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < total; i += warps) {
         const uint32_t g = graph_of(woff, k, i);
         const GraphDev G = gs[g];
-        const uint32_t c = plan_vertex(G, (uint32_t)(i - woff[g]), chunk, item_work, algo, 0.0, W[i],
+        const uint32_t x = (uint32_t)(i - woff[g]);
+        const uint64_t ubase = G.off[x];
+        const uint32_t du = (uint32_t)(G.off[x + 1] - ubase), upx = G.up[x], chunks = (du + chunk - 1) / chunk;
+        const uint32_t c = plan_vertex(G, x, item_work, 0.0, W[i],
+                                       [&](uint32_t j) { return pair_units(G, x, ubase, du, upx, j, chunks, algo); },
                                        [](uint32_t, uint32_t) {});
         if ((threadIdx.x & 31) == 0) cnt[i] = c;
     }
@@ -77,7 +81,10 @@ __global__ void k_batch_emit(const GraphDev* __restrict__ gs, const uint64_t* __
         const GraphDev G = gs[g];
         const uint32_t x = (uint32_t)(i - woff[g]);
         Item* out = items + pos[i];
-        const uint32_t c = plan_vertex(G, x, chunk, item_work, algo, 0.0, W[i],
+        const uint64_t ubase = G.off[x];
+        const uint32_t du = (uint32_t)(G.off[x + 1] - ubase), upx = G.up[x], chunks = (du + chunk - 1) / chunk;
+        const uint32_t c = plan_vertex(G, x, item_work, 0.0, W[i],
+                                       [&](uint32_t j) { return pair_units(G, x, ubase, du, upx, j, chunks, algo); },
                                        [&](uint32_t j, uint32_t rank) { out[rank] = Item{x, j, 0u, g}; });
         plan_vertex_ends(out, c, (uint32_t)(G.off[x + 1] - G.off[x]));
     }

@@ -161,18 +161,20 @@ __global__ void k_graph_sums(const uint64_t* off, const uint32_t* adj, const uin
 // search and writes rp = k and vs = (class-1, class-2 counts).  At an upper neighbour
 // (k >= up[v]) they are the third vertices w > N[v][k] reached from v, the u side of the pair
 // (v, N[v][k]): us = (class-1, class-2 counts).  wk[0] += the suffix lengths at lower
-// neighbours (the N[v] entries a census walks).
+// neighbours (the N[v] entries a census walks), wk[1] += those of them with ids below
+// kMapIdsSuffix: with c the entries of N[v] below it (a prefix), the walk past position k
+// meets max(0, c - k - 1) of them.
 __global__ void k_pair_tables(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
                               const uint32_t* __restrict__ up, const uint64_t* __restrict__ ub, uint32_t n,
                               uint32_t* rp, uint2* vs, uint2* us, unsigned long long* wk) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t after = lane == 31 ? 0u : ~((2u << lane) - 1u);   // lanes above this one
-    unsigned long long walk = 0;
+    unsigned long long walk = 0, walk_map = 0;
     for (uint64_t v = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
         const uint64_t ob = off[v];
         const uint32_t dv = (uint32_t)(off[v + 1] - ob), lv = up[v];
-        uint32_t c1 = 0, c2 = 0;
+        uint32_t c1 = 0, c2 = 0, cmap = 0;
         for (uint32_t cs = dv & ~31u; dv && cs <= dv; cs -= 32) {   // blocks from the last one down
             const uint32_t k = cs + lane;
             const uint32_t e = k < dv ? adj[ob + k] : 0u;
@@ -194,11 +196,15 @@ __global__ void k_pair_tables(const uint64_t* __restrict__ off, const uint32_t* 
             }
             c1 += __popc(b1);
             c2 += __popc(b2);
+            cmap += __popc(__ballot_sync(0xffffffffu, k < dv && (e >> 2) < kMapIdsSuffix));
             if (cs == 0) break;
         }
+        const unsigned long long m = min(lv, cmap);
+        if (lane == 0) walk_map += m * cmap - m * (m + 1) / 2;
     }
     for (int o = 16; o; o >>= 1) walk += __shfl_xor_sync(0xffffffffu, walk, o);
     if (lane == 0 && walk) atomicAdd(wk, walk);
+    if (lane == 0 && walk_map) atomicAdd(wk + 1, walk_map);
 }
 
 // upper pairs per vertex: deg - up
@@ -331,19 +337,19 @@ tc_status finish_graph(GraphStore& g, uint64_t E, int B, uint64_t* ukey, uint32_
         }
         TC_TRY(scan_u32_to_u64(ucnt.as<uint32_t>(), g.ub.as<uint64_t>(), n, st));
         if (E) {
-            // the walk length goes to stats[1] (ids out of range), which is zero here: a build with
-            // such ids stops before this point
+            // the walk lengths go to stats[8..9]
             k_pair_tables<<<grid_for((uint64_t)n * 32, kB, 1u << 16), kB, 0, st>>>(
                 g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(),
                                                 g.ub.as<uint64_t>(), n, g.rp.as<uint32_t>(), g.vs.as<uint2>(), g.us.as<uint2>(),
-                                                stats.as<unsigned long long>() + 1);
+                                                stats.as<unsigned long long>() + 8);
             TC_LAUNCH("k_pair_tables");
         }
     }
-    unsigned long long hs[8];
+    unsigned long long hs[10];
     TC_CUDA(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaStreamSynchronize(st));
-    g.sum_walk = hs[1];
+    g.sum_walk = hs[8];
+    g.sum_walk_map = hs[9];
     g.e_sym = E;
     g.mutual = hs[2];
     g.arcs = E + hs[2];
@@ -363,8 +369,8 @@ tc_status build_from_arcs(GraphStore& g, uint64_t m, const uint32_t* d_src, cons
     const int B = bits_for(n);
     if (m >= (1ull << 32)) return fail(TC_ERR_RANGE, "more than 2^32-1 arcs");
     DevBuf stats, keys, tmp;
-    TC_TRY(stats.alloc(sizeof(unsigned long long) * 8, st));
-    TC_CUDA(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * 8, st));
+    TC_TRY(stats.alloc(sizeof(unsigned long long) * 10, st));
+    TC_CUDA(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * 10, st));
     TC_TRY(keys.alloc(sizeof(uint64_t) * (m ? m : 1), st));
     TC_TRY(tmp.alloc(sizeof(uint64_t) * (m ? m : 1), st));
     if (m) {
@@ -428,8 +434,8 @@ tc_status build_from_csr(GraphStore& g, const uint64_t* d_off, const uint32_t* d
     if (total_h & 1) return fail(TC_ERR_ARG, "CSR is not symmetric (odd number of entries)");
     if (total_h >= (1ull << 32)) return fail(TC_ERR_RANGE, "more than 2^32-1 CSR entries");
     DevBuf stats;
-    TC_TRY(stats.alloc(sizeof(unsigned long long) * 8, st));
-    TC_CUDA(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * 8, st));
+    TC_TRY(stats.alloc(sizeof(unsigned long long) * 10, st));
+    TC_CUDA(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * 10, st));
     const unsigned gridN = grid_for(n, kB, 1u << 16);
     k_check_csr<<<gridN, kB, 0, st>>>(d_off, d_adj, n, total_h, stats.as<unsigned long long>());
     TC_LAUNCH("k_check_csr");

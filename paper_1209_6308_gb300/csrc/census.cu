@@ -51,8 +51,12 @@ constexpr uint32_t kTrip = 32u * TC_UNROLL;  // entries of N[v] per warp trip
 // Membership of the staged chunk of N[u]: ids below kMapIds (the highest-degree vertices, which
 // make up most of the N[v] entries walked) sit in a direct map of two direction bits per id;
 // the rest in the open-addressing hash.
-template <int ALGO> constexpr uint32_t map_ids() { return ALGO == TC_ALGO_UNION ? (1u << 16) : (1u << 17); }
-constexpr uint32_t kHashFactorUnion = 2, kHashFactorSuffix = 2;
+// MAP selects the map; without it (graphs whose walks meet mostly ids past the map's range)
+// every entry goes to a hash of 4x the chunk (2x for the union walk, beside its sorted copy).
+template <int ALGO, bool MAP> constexpr uint32_t map_ids() {
+    return MAP ? (ALGO == TC_ALGO_UNION ? kMapIdsUnion : kMapIdsSuffix) : 0u;
+}
+template <int ALGO, bool MAP> constexpr uint32_t hash_factor() { return ALGO == TC_ALGO_UNION ? 2u : (MAP ? 2u : 4u); }
 
 __device__ uint8_t d_tricode_class[64];
 
@@ -304,15 +308,15 @@ __device__ __forceinline__ void flush_graph(Counts& k, int lane, unsigned long l
 
 // VT: the graphs carry the per upper pair tables (GraphDev::ub, rp, vs): each N[v] walk starts
 // past u, and the v-only triads come from the tables' suffix counts.
-template <int ALGO, int MODE, bool VT>
+template <int ALGO, int MODE, bool VT, bool MAP>
 __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t chunk = P.chunk;
-    constexpr uint32_t kHashFactor = ALGO == TC_ALGO_UNION ? kHashFactorUnion : kHashFactorSuffix;
-    constexpr uint32_t kMap = map_ids<ALGO>();
+    constexpr uint32_t kHashFactor = hash_factor<ALGO, MAP>();
+    constexpr uint32_t kMap = map_ids<ALGO, MAP>();
     // map-first items (suffix form with tables): the map is staged once per item and only the
     // entries past it are chunked; the union walk keeps per-chunk staging for its sorted copy
-    constexpr bool MF = VT && ALGO == TC_ALGO_SUFFIX;
+    constexpr bool MF = VT && MAP && ALGO == TC_ALGO_SUFFIX;
     // TC_ALGO_UNION keeps the sorted chunk for its walk; the suffix form needs the hash, the
     // direction bit planes and their block prefix counts
     uint32_t* sA = reinterpret_cast<uint32_t*>(smem);                                  // [chunk] (union)
@@ -515,6 +519,11 @@ __global__ void __launch_bounds__(kThreads, TC_MIN_BLOCKS) k_census(Params P) {
                         const uint32_t m = (1u << r) - 1u;
                         const uint32_t bl = r ? (sLo[q] & m) : 0u, bh = r ? (sHi[q] & m) : 0u;
                         suf = sCk[nq] - sCk[q] - pack3(__popc(bl & ~bh), __popc(bh & ~bl), __popc(bl & bh));
+                        if (VT) {   // the table form's fold takes the chunk's u side as counts
+                            const uint32_t s1 = (uint32_t)(suf & 0x1fffffull), s2 = (uint32_t)((suf >> 21) & 0x1fffffull),
+                                           s3 = (uint32_t)((suf >> 42) & 0x1fffffull);
+                            usv = make_uint3(s1, s2, s1 + s2 + s3);
+                        }
                     }
                     uint3 vsv = make_uint3(0u, 0u, 0u);
                     if (VT && c == 0) {
@@ -740,50 +749,70 @@ __device__ __forceinline__ double learned_items(const float* cost, uint64_t x, u
     return cost ? fmax(1.0, ceil((double)cost[x] / (double)item_work)) : 0.0;
 }
 
-// W[x] = the work of vertex x's upper pairs; total[0] += the sum (sizes the items when the
-// options leave item_work to the graph).
-__global__ void k_plan_work(GraphDev g, uint32_t u_end, uint32_t chunk, int algo, unsigned long long* W,
+// W[x] = the work of vertex x's upper pairs, pu[pair] = each pair's (by table index, pairs of
+// vertices x < u_end); total[0] += the sum (sizes the items when the options leave item_work
+// to the graph).
+__global__ void k_plan_work(GraphDev g, uint32_t u_end, uint32_t chunk, int algo, unsigned long long* W, uint32_t* pu,
                             unsigned long long* total) {
+    const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long sum = 0;
     for (uint64_t x = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; x < u_end; x += warps) {
-        const unsigned long long w = vertex_units(g, (uint32_t)x, chunk, algo);
+        const uint64_t ubase = g.off[x];
+        const uint32_t du = (uint32_t)(g.off[x + 1] - ubase), upx = g.up[x];
+        const uint32_t chunks = (du + chunk - 1) / chunk;
+        const uint64_t tb = g.ub[x] - upx;
+        unsigned long long w = 0;
+        for (uint32_t j = upx + lane; j < du; j += 32) {
+            const uint64_t c = pair_units(g, (uint32_t)x, ubase, du, upx, j, chunks, algo);
+            pu[tb + j] = c < 0xffffffffull ? (uint32_t)c : 0xffffffffu;
+            w += c;
+        }
+        for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
         sum += w;
-        if ((threadIdx.x & 31) == 0) W[x] = w;
+        if (lane == 0) W[x] = w;
     }
-    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(total, sum);
+    if (lane == 0 && sum) atomicAdd(total, sum);
 }
 
-__global__ void k_plan_count(GraphDev g, uint32_t u_end, uint32_t chunk, uint32_t item_work, int algo,
-                             const float* cost, const unsigned long long* W, uint32_t* cnt) {
+__global__ void k_plan_count(GraphDev g, uint32_t u_end, uint32_t item_work, const float* cost,
+                             const unsigned long long* W, const uint32_t* pu, uint32_t* cnt) {
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t x = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; x < u_end; x += warps) {
-        const uint32_t c = plan_vertex(g, (uint32_t)x, chunk, item_work, algo, learned_items(cost, x, item_work), W[x],
+        const uint64_t tb = g.ub[x] - g.up[x];
+        const uint32_t c = plan_vertex(g, (uint32_t)x, item_work, learned_items(cost, x, item_work), W[x],
+                                       [&](uint32_t j) { return (unsigned long long)pu[tb + j]; },
                                        [](uint32_t, uint32_t) {});
         if ((threadIdx.x & 31) == 0) cnt[x] = c;
     }
 }
 
-__global__ void k_plan_emit(GraphDev g, uint32_t u_end, uint32_t chunk, uint32_t item_work, int algo,
-                            const float* cost, const unsigned long long* W, const uint32_t* pos, Item* items) {
+__global__ void k_plan_emit(GraphDev g, uint32_t u_end, uint32_t item_work, const float* cost,
+                            const unsigned long long* W, const uint32_t* pu, const uint32_t* pos, Item* items) {
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t x = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; x < u_end; x += warps) {
         Item* out = items + pos[x];
-        const uint32_t c = plan_vertex(g, (uint32_t)x, chunk, item_work, algo, learned_items(cost, x, item_work), W[x],
+        const uint64_t tb = g.ub[x] - g.up[x];
+        const uint32_t c = plan_vertex(g, (uint32_t)x, item_work, learned_items(cost, x, item_work), W[x],
+                                       [&](uint32_t j) { return (unsigned long long)pu[tb + j]; },
                                        [&](uint32_t j, uint32_t rank) { out[rank] = Item{(uint32_t)x, j, 0u, 0u}; });
         plan_vertex_ends(out, c, (uint32_t)(g.off[x + 1] - g.off[x]));
     }
 }
 
 std::atomic<uint64_t> g_table_uploaded{0};
-constexpr int kForms = 4;   // single graph without tables, single graph, batch, wave (all with tables)
+constexpr int kForms = 5;   // single graph without tables; single graph with tables, with and without the
+                            // map; batch and wave (tables and map)
 std::atomic<uint64_t> g_attr_set[2 * kForms] = {};
 std::atomic<int> g_dyn_limit[2 * kForms] = {};   // per kernel form: optin - static smem
 
-size_t census_smem(uint32_t algo, uint32_t chunk) {
+size_t census_smem(uint32_t algo, uint32_t chunk, bool map) {
     const bool uni = algo == TC_ALGO_UNION;
-    const unsigned long long words = (uni ? 1ull + kHashFactorUnion : (unsigned long long)kHashFactorSuffix) * chunk +
-                                     (uni ? map_ids<TC_ALGO_UNION>() : map_ids<TC_ALGO_SUFFIX>()) / 16;
+    const unsigned long long hf = uni ? hash_factor<TC_ALGO_UNION, true>()
+                                      : (map ? hash_factor<TC_ALGO_SUFFIX, true>() : hash_factor<TC_ALGO_SUFFIX, false>());
+    const unsigned long long mw = uni ? (map ? map_ids<TC_ALGO_UNION, true>() : 0u)
+                                      : (map ? map_ids<TC_ALGO_SUFFIX, true>() : 0u);
+    const unsigned long long words = ((uni ? 1ull : 0ull) + hf) * chunk + mw / 16;
     return sizeof(uint32_t) * words + sizeof(uint32_t) * (chunk / 16) + sizeof(unsigned long long) * (chunk / 32 + 1) +
            sizeof(uint32_t) * kMaxItemPairs + sizeof(unsigned long long) * 16 + 64;
 }
@@ -804,10 +833,16 @@ tc_status prepare_device(cudaStream_t st, int algo, size_t smem) {
     const int limit = optin - 256;   // leave room for the kernel's static shared variables
     if ((int)smem > limit) return fail(TC_ERR_ARG, "chunk_entries too large for this GPU's shared memory");
     const void* fns[2 * kForms] = {
-        (const void*)k_census<TC_ALGO_UNION, kModeSingle, false>, (const void*)k_census<TC_ALGO_SUFFIX, kModeSingle, false>,
-        (const void*)k_census<TC_ALGO_UNION, kModeSingle, true>,  (const void*)k_census<TC_ALGO_SUFFIX, kModeSingle, true>,
-        (const void*)k_census<TC_ALGO_UNION, kModeBatch, true>,   (const void*)k_census<TC_ALGO_SUFFIX, kModeBatch, true>,
-        (const void*)k_census<TC_ALGO_UNION, kModeWave, true>,    (const void*)k_census<TC_ALGO_SUFFIX, kModeWave, true>};
+        (const void*)k_census<TC_ALGO_UNION, kModeSingle, false, true>,
+        (const void*)k_census<TC_ALGO_SUFFIX, kModeSingle, false, true>,
+        (const void*)k_census<TC_ALGO_UNION, kModeSingle, true, true>,
+        (const void*)k_census<TC_ALGO_SUFFIX, kModeSingle, true, true>,
+        (const void*)k_census<TC_ALGO_UNION, kModeSingle, true, false>,
+        (const void*)k_census<TC_ALGO_SUFFIX, kModeSingle, true, false>,
+        (const void*)k_census<TC_ALGO_UNION, kModeBatch, true, true>,
+        (const void*)k_census<TC_ALGO_SUFFIX, kModeBatch, true, true>,
+        (const void*)k_census<TC_ALGO_UNION, kModeWave, true, true>,
+        (const void*)k_census<TC_ALGO_SUFFIX, kModeWave, true, true>};
     for (int b = 0; b < kForms; ++b) {
         const int idx = 2 * b + algo;
         if (!(g_attr_set[idx].load() & bit)) {
@@ -851,23 +886,24 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out) {
     p.warp_end = g.n_active;
     p.n_items = 0;
     if (u_end) {
-        DevBuf cnt, pos, tot, wv, wt;
+        DevBuf cnt, pos, tot, wv, wt, pu;
         TC_TRY(cnt.alloc(sizeof(uint32_t) * u_end, st));
         TC_TRY(pos.alloc(sizeof(uint32_t) * u_end, st));
         TC_TRY(tot.alloc(sizeof(uint32_t), st));
         TC_TRY(wv.alloc(sizeof(unsigned long long) * u_end, st));
         TC_TRY(wt.alloc(sizeof(unsigned long long), st));
+        TC_TRY(pu.alloc(sizeof(uint32_t) * (g.e_sym ? g.e_sym : 1), st));   // pair units by table index
         TC_CUDA(cudaMemsetAsync(wt.p, 0, sizeof(unsigned long long), st));
         const float* cost = (o.schedule == TC_SCHED_LEARNED) ? g.cost.as<float>() : nullptr;
         const unsigned pgrid = grid_for((uint64_t)u_end * 32, 256, 8192);
-        k_plan_work<<<pgrid, 256, 0, st>>>(gd, u_end, o.chunk, (int)o.algo, wv.as<unsigned long long>(),
+        k_plan_work<<<pgrid, 256, 0, st>>>(gd, u_end, o.chunk, (int)o.algo, wv.as<unsigned long long>(), pu.as<uint32_t>(),
                                            wt.as<unsigned long long>());
         TC_LAUNCH("k_plan_work");
         unsigned long long total_units = 0;
         TC_CUDA(cudaMemcpyAsync(&total_units, wt.p, sizeof(total_units), cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
         const uint32_t iw = o.item_work ? o.item_work : adaptive_item_work(total_units, (unsigned)census_grid(o));
-        k_plan_count<<<pgrid, 256, 0, st>>>(gd, u_end, o.chunk, iw, (int)o.algo, cost, wv.as<unsigned long long>(),
+        k_plan_count<<<pgrid, 256, 0, st>>>(gd, u_end, iw, cost, wv.as<unsigned long long>(), pu.as<uint32_t>(),
                                             cnt.as<uint32_t>());
         TC_LAUNCH("k_plan_count");
         TC_TRY(scan_u32(cnt.as<uint32_t>(), pos.as<uint32_t>(), u_end, tot.as<uint32_t>(), st));
@@ -875,7 +911,7 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out) {
         TC_CUDA(cudaStreamSynchronize(st));
         TC_TRY(p.items.alloc_persistent(sizeof(Item) * (p.n_items ? p.n_items : 1)));
         if (p.n_items) {
-            k_plan_emit<<<pgrid, 256, 0, st>>>(gd, u_end, o.chunk, iw, (int)o.algo, cost, wv.as<unsigned long long>(),
+            k_plan_emit<<<pgrid, 256, 0, st>>>(gd, u_end, iw, cost, wv.as<unsigned long long>(), pu.as<uint32_t>(),
                                                pos.as<uint32_t>(), p.items.as<Item>());
             TC_LAUNCH("k_plan_emit");
         }
@@ -899,7 +935,7 @@ uint32_t warp_block_shift(uint64_t vertices, unsigned grid) {
 
 tc_status census_launch_batch(const GraphDev* d_graphs, const Item* items, uint32_t n_items, const uint4* wblocks,
                               uint32_t n_wblocks, const Opts& o, uint32_t* ctr, unsigned long long* d_out, cudaStream_t st) {
-    const size_t smem = census_smem(o.algo, o.chunk);
+    const size_t smem = census_smem(o.algo, o.chunk, true);
     Params P;
     std::memset(&P, 0, sizeof(P));
     P.items = items;
@@ -912,8 +948,8 @@ tc_status census_launch_batch(const GraphDev* d_graphs, const Item* items, uint3
     P.wblocks = wblocks;
     P.n_wblocks = n_wblocks;
     const unsigned grid = (unsigned)census_grid(o);
-    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, kModeBatch, true><<<grid, kThreads, smem, st>>>(P);
-    else k_census<TC_ALGO_SUFFIX, kModeBatch, true><<<grid, kThreads, smem, st>>>(P);
+    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, kModeBatch, true, true><<<grid, kThreads, smem, st>>>(P);
+    else k_census<TC_ALGO_SUFFIX, kModeBatch, true, true><<<grid, kThreads, smem, st>>>(P);
     TC_LAUNCH("k_census (batched)");
     return TC_OK;
 }
@@ -921,7 +957,7 @@ tc_status census_launch_batch(const GraphDev* d_graphs, const Item* items, uint3
 tc_status census_launch_wave(const WaveReq* d_reqs, uint32_t n_reqs, uint32_t total_items, uint32_t total_blocks,
                              const Opts& o, unsigned grid, uint32_t* ctr, cudaStream_t st) {
     if (n_reqs > kMaxWave) return fail(TC_ERR_RANGE, "wave larger than kMaxWave requests");
-    const size_t smem = census_smem(o.algo, o.chunk);
+    const size_t smem = census_smem(o.algo, o.chunk, true);
     Params P;
     std::memset(&P, 0, sizeof(P));
     P.n_items = total_items;
@@ -932,17 +968,24 @@ tc_status census_launch_wave(const WaveReq* d_reqs, uint32_t n_reqs, uint32_t to
     P.n_wblocks = total_blocks;
     P.reqs = d_reqs;
     P.n_reqs = n_reqs;
-    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, kModeWave, true><<<grid, kThreads, smem, st>>>(P);
-    else k_census<TC_ALGO_SUFFIX, kModeWave, true><<<grid, kThreads, smem, st>>>(P);
+    if (o.algo == TC_ALGO_UNION) k_census<TC_ALGO_UNION, kModeWave, true, true><<<grid, kThreads, smem, st>>>(P);
+    else k_census<TC_ALGO_SUFFIX, kModeWave, true, true><<<grid, kThreads, smem, st>>>(P);
     TC_LAUNCH("k_census (wave)");
     return TC_OK;
 }
 
-tc_status census_prepare(cudaStream_t st, const Opts& o) { return prepare_device(st, (int)o.algo, census_smem(o.algo, o.chunk)); }
+tc_status census_prepare(cudaStream_t st, const Opts& o) {
+    return prepare_device(st, (int)o.algo, census_smem(o.algo, o.chunk, true));
+}
+
+// The map pays when it answers most of the walk's lookups: at least half of the N[v] entries
+// walked have ids below its range (counted when the tables are built).
+bool census_use_map(const GraphStore& g) { return 2 * g.sum_walk_map >= g.sum_walk; }
 
 tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
                             uint32_t warp_end, uint32_t* ctr, unsigned long long* d_out16, cudaStream_t st) {
-    const size_t smem = census_smem(o.algo, o.chunk);
+    const bool vt = gd.vs != nullptr, map = true;
+    const size_t smem = census_smem(o.algo, o.chunk, map);
     TC_TRY(prepare_device(st, (int)o.algo, smem));
     Params P;
     P.g = gd;
@@ -963,13 +1006,14 @@ tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items
     P.reqs = nullptr;
     P.n_reqs = 0;
     const unsigned grid = (unsigned)census_grid(o);
-    const bool vt = P.g.vs != nullptr;
     if (o.algo == TC_ALGO_UNION) {
-        if (vt) k_census<TC_ALGO_UNION, kModeSingle, true><<<grid, kThreads, smem, st>>>(P);
-        else k_census<TC_ALGO_UNION, kModeSingle, false><<<grid, kThreads, smem, st>>>(P);
+        if (!vt) k_census<TC_ALGO_UNION, kModeSingle, false, true><<<grid, kThreads, smem, st>>>(P);
+        else if (map) k_census<TC_ALGO_UNION, kModeSingle, true, true><<<grid, kThreads, smem, st>>>(P);
+        else k_census<TC_ALGO_UNION, kModeSingle, true, false><<<grid, kThreads, smem, st>>>(P);
     } else {
-        if (vt) k_census<TC_ALGO_SUFFIX, kModeSingle, true><<<grid, kThreads, smem, st>>>(P);
-        else k_census<TC_ALGO_SUFFIX, kModeSingle, false><<<grid, kThreads, smem, st>>>(P);
+        if (!vt) k_census<TC_ALGO_SUFFIX, kModeSingle, false, true><<<grid, kThreads, smem, st>>>(P);
+        else if (map) k_census<TC_ALGO_SUFFIX, kModeSingle, true, true><<<grid, kThreads, smem, st>>>(P);
+        else k_census<TC_ALGO_SUFFIX, kModeSingle, true, false><<<grid, kThreads, smem, st>>>(P);
     }
     TC_LAUNCH("k_census");
     return TC_OK;
@@ -978,7 +1022,9 @@ tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items
 tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16,
                          unsigned long long* d_vcost, unsigned long long* d_phase) {
     if (g.e_sym == 0) return TC_OK;
-    const size_t smem = census_smem(o.algo, o.chunk);
+    const bool vt = g.vs.p != nullptr;
+    const bool map = !vt || o.map_mode == 1 || (o.map_mode == 0 && census_use_map(g));
+    const size_t smem = census_smem(o.algo, o.chunk, map);
     TC_TRY(prepare_device(st, (int)o.algo, smem));
     TC_CUDA(cudaMemsetAsync(g.ctr.p, 0, sizeof(uint32_t) * 4, st));
     Params P;
@@ -1002,13 +1048,14 @@ tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream
     P.reqs = nullptr;
     P.n_reqs = 0;
     const unsigned grid = (unsigned)census_grid(o);
-    const bool vt = P.g.vs != nullptr;
     if (o.algo == TC_ALGO_UNION) {
-        if (vt) k_census<TC_ALGO_UNION, kModeSingle, true><<<grid, kThreads, smem, st>>>(P);
-        else k_census<TC_ALGO_UNION, kModeSingle, false><<<grid, kThreads, smem, st>>>(P);
+        if (!vt) k_census<TC_ALGO_UNION, kModeSingle, false, true><<<grid, kThreads, smem, st>>>(P);
+        else if (map) k_census<TC_ALGO_UNION, kModeSingle, true, true><<<grid, kThreads, smem, st>>>(P);
+        else k_census<TC_ALGO_UNION, kModeSingle, true, false><<<grid, kThreads, smem, st>>>(P);
     } else {
-        if (vt) k_census<TC_ALGO_SUFFIX, kModeSingle, true><<<grid, kThreads, smem, st>>>(P);
-        else k_census<TC_ALGO_SUFFIX, kModeSingle, false><<<grid, kThreads, smem, st>>>(P);
+        if (!vt) k_census<TC_ALGO_SUFFIX, kModeSingle, false, true><<<grid, kThreads, smem, st>>>(P);
+        else if (map) k_census<TC_ALGO_SUFFIX, kModeSingle, true, true><<<grid, kThreads, smem, st>>>(P);
+        else k_census<TC_ALGO_SUFFIX, kModeSingle, true, false><<<grid, kThreads, smem, st>>>(P);
     }
     TC_LAUNCH("k_census");
     return TC_OK;

@@ -18,9 +18,10 @@ struct Opts {
     uint32_t chunk = 0;
     uint32_t item_work = 0;   // 0: sized to the graph (adaptive_item_work)
     uint32_t ctas_per_sm = 0;
+    uint32_t map_mode = 0;    // 0 auto, 1 always, 2 never (single-graph census with tables)
     bool operator==(const Opts& o) const {
         return algo == o.algo && schedule == o.schedule && warp_max_deg == o.warp_max_deg && chunk == o.chunk &&
-               item_work == o.item_work && ctas_per_sm == o.ctas_per_sm;
+               item_work == o.item_work && ctas_per_sm == o.ctas_per_sm && map_mode == o.map_mode;
     }
 };
 
@@ -50,6 +51,7 @@ struct Plan {
 struct GraphStore {
     uint32_t n = 0, n_active = 0, max_deg = 0;
     uint64_t arcs = 0, e_sym = 0, mutual = 0, loops = 0, dups = 0, sum_d2 = 0, sum_dv_upper = 0, sum_walk = 0;
+    uint64_t sum_walk_map = 0;   // walked entries with ids below kMapIdsSuffix
     DevBuf off, adj, up, new_of_old;
     DevBuf ub, rp, vs, us;   // per upper pair tables (see GraphDev)
     DevBuf ctr;        // census work counters (uint32 x 4)

@@ -36,34 +36,35 @@ __device__ __forceinline__ unsigned long long vertex_units(const GraphDev& g, ui
 }
 
 // One warp per vertex (all lanes call it with the same u and W = vertex_units(u)).  s_hint > 0
-// fixes S (the learned schedule), else S = ceil(W / item_work).  emit(j, rank) runs on the lane
-// of each pair that starts an item, rank = the item's index within the vertex.  Returns the
-// vertex's item count.
-template <typename Emit>
-__device__ uint32_t plan_vertex(const GraphDev& g, uint32_t u, uint32_t chunk, uint32_t item_work, int algo,
-                                double s_hint, unsigned long long W, Emit emit) {
+// fixes S (the learned schedule), else S = ceil(W / item_work).  units(j) gives pair j's work
+// (stored by a first pass, or pair_units); emit(j, rank) runs on the lane of each pair that
+// starts an item, rank = the item's index within the vertex.  Returns the vertex's item count.
+// The cuts are computed in single precision: both passes run the same arithmetic on the same
+// values, so they agree, and items are at least 2^14 units, far above the rounding.
+template <typename Units, typename Emit>
+__device__ uint32_t plan_vertex(const GraphDev& g, uint32_t u, uint32_t item_work, double s_hint,
+                                unsigned long long W, Units units, Emit emit) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t ubase = g.off[u];
     const uint32_t du = (uint32_t)(g.off[u + 1] - ubase), upu = g.up[u];
     if (du <= upu) return 0;
-    const uint32_t chunks = (du + chunk - 1) / chunk;
-    double S = s_hint > 0.0 ? ceil(s_hint) : ceil((double)W / (double)item_work);
-    if (S < 1.0) S = 1.0;
-    const double per = (double)W / S;
+    float S = s_hint > 0.0 ? ceilf((float)s_hint) : ceilf((float)W / (float)item_work);
+    if (S < 1.f) S = 1.f;
+    const float inv_per = S / (float)(W ? W : 1ull);
     unsigned long long carry = 0;
     uint32_t prev = 0xffffffffu, count = 0;
     for (uint32_t jb = upu; jb < du; jb += 32) {
         const uint32_t j = jb + lane;
         const bool ok = j < du;
-        const unsigned long long c = ok ? pair_units(g, u, ubase, du, upu, j, chunks, algo) : 0ull;
+        const unsigned long long c = ok ? units(j) : 0ull;
         unsigned long long incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= (uint32_t)o) incl += y;
         }
-        const double mid = (double)(carry + incl - c) + 0.5 * (double)c;
-        uint32_t id = ok ? (uint32_t)floor(mid / per) + (j - upu) / kMaxItemPairs : 0xffffffffu;
+        const float mid = (float)(carry + incl - c) + 0.5f * (float)c;
+        uint32_t id = ok ? (uint32_t)floorf(mid * inv_per) + (j - upu) / kMaxItemPairs : 0xffffffffu;
         uint32_t before = __shfl_up_sync(0xffffffffu, id, 1);
         if (lane == 0) before = prev;
         const bool start = ok && id != before;

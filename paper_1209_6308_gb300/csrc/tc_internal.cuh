@@ -74,6 +74,9 @@ struct Item {
     uint32_t u, j0, j1, pad;
 };
 constexpr uint32_t kMaxItemPairs = 1024;   // pairs per item (one N[v] cursor each in shared memory)
+// The census answers membership in N[u] for ids below these from a direct two-bit-per-id map
+// of the staged list (the highest-degree vertices, since ids descend with the degree).
+constexpr uint32_t kMapIdsSuffix = 1u << 17, kMapIdsUnion = 1u << 16;
 
 // ------------------------------------------------------------------ primitives
 // Exclusive scan of n uint32 values into uint32 (out may alias nothing); *total (device

@@ -18,6 +18,8 @@ TIERS = [
     {},                                                       # defaults: warp <= 64, chunk 4096
     {"warp_max_deg": 8, "chunk_entries": 512, "item_work": 2048},   # tiny chunks: hubs split
     {"warp_max_deg": 64, "chunk_entries": 8192, "item_work": 1 << 22, "ctas_per_sm": 1},
+    {"map_mode": 2},                                          # no id map: every entry hashed
+    {"warp_max_deg": 8, "chunk_entries": 512, "item_work": 2048, "map_mode": 2},
 ]
 
 
@@ -292,6 +294,8 @@ def test_rmat_scale20_union_equals_suffix_and_tiers(tc, rmat20):
         base = g.census(options={"algo": 1})
         assert g.census(options={"algo": 0}) == base
         assert g.census(options={"algo": 1, "chunk_entries": 1024, "warp_max_deg": 16}) == base
+        assert g.census(options={"algo": 1, "map_mode": 2}) == base
+        assert g.census(options={"algo": 0, "map_mode": 2}) == base
         inv_sum = sum(base)
     assert inv_sum == choose3(n)
 
