@@ -86,7 +86,7 @@ __global__ void k_batch_emit(const GraphDev* __restrict__ gs, const uint64_t* __
         const uint32_t c = plan_vertex(G, x, item_work, 0.0, W[i],
                                        [&](uint32_t j) { return pair_units(G, x, ubase, du, upx, j, chunks, algo); },
                                        [&](uint32_t j, uint32_t rank) { out[rank] = Item{x, j, 0u, g}; });
-        plan_vertex_ends(out, c, (uint32_t)(G.off[x + 1] - G.off[x]));
+        plan_ends(out, c, (uint32_t)(G.off[x + 1] - G.off[x]));
     }
 }
 

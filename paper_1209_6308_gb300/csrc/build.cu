@@ -153,7 +153,11 @@ __global__ void k_graph_sums(const uint64_t* off, const uint32_t* adj, const uin
     }
 }
 
-// Per upper pair tables.  One warp per vertex v takes N[v] in 32-entry blocks from the end,
+constexpr uint32_t kLongList = 4096;   // longer lists: k_pair_tables_long, a CTA per vertex
+constexpr int kLongThreads = 1024;
+
+// Per upper pair tables.  One warp per vertex v (lists of at most kLongList entries; longer ones
+// are k_pair_tables_long's) takes N[v] in 32-entry blocks from the end,
 // keeping running counts of the direction classes of the entries behind the block and adding,
 // per lane, the block's entries after its own by ballot: so the lane at position k knows the
 // counts of the entries after k.  At a lower neighbour u = N[v][k] (k < up[v]) those are the
@@ -174,6 +178,7 @@ __global__ void k_pair_tables(const uint64_t* __restrict__ off, const uint32_t* 
     for (uint64_t v = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
         const uint64_t ob = off[v];
         const uint32_t dv = (uint32_t)(off[v + 1] - ob), lv = up[v];
+        if (dv > kLongList) continue;                                 // k_pair_tables_long's
         uint32_t c1 = 0, c2 = 0, cmap = 0;
         for (uint32_t cs = dv & ~31u; dv && cs <= dv; cs -= 32) {   // blocks from the last one down
             const uint32_t k = cs + lane;
@@ -205,6 +210,84 @@ __global__ void k_pair_tables(const uint64_t* __restrict__ off, const uint32_t* 
     for (int o = 16; o; o >>= 1) walk += __shfl_xor_sync(0xffffffffu, walk, o);
     if (lane == 0 && walk) atomicAdd(wk, walk);
     if (lane == 0 && walk_map) atomicAdd(wk + 1, walk_map);
+}
+
+// The same tables for the vertices with more than kLongList entries, a prefix of the ids
+// (degrees descend), one CTA per vertex: a warp per list walks at most kLongList / 32 blocks in
+// series.  Each warp takes a contiguous segment of N[v] (a multiple of 32 entries), counts its
+// class-1 and class-2 entries, and then walks it backward from the counts of the segments after
+// it, as k_pair_tables walks a whole list.
+__global__ void __launch_bounds__(kLongThreads) k_pair_tables_long(
+        const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj, const uint32_t* __restrict__ up,
+        const uint64_t* __restrict__ ub, uint32_t n, uint32_t* rp, uint2* vs, uint2* us, unsigned long long* wk) {
+    __shared__ uint32_t s_c1[kLongThreads / 32], s_c2[kLongThreads / 32], s_map[kLongThreads / 32];
+    const uint64_t v = blockIdx.x;
+    if (v >= n) return;
+    const uint64_t ob = off[v];
+    const uint32_t dv = (uint32_t)(off[v + 1] - ob), lv = up[v];
+    if (dv <= kLongList) return;                                      // the same for the whole CTA
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t after = lane == 31 ? 0u : ~((2u << lane) - 1u);
+    const uint32_t seg = ((dv + nw - 1) / nw + 31u) & ~31u;
+    const uint32_t s0 = min(dv, wid * seg), s1 = min(dv, s0 + seg);
+    uint32_t a1 = 0, a2 = 0, am = 0;
+#pragma unroll 4
+    for (uint32_t k = s0 + lane; k < s1; k += 32) {
+        const uint32_t e = adj[ob + k];
+        a1 += (e & 3u) == 1u;
+        a2 += (e & 3u) == 2u;
+        am += (e >> 2) < kMapIdsSuffix;
+    }
+    a1 = __reduce_add_sync(0xffffffffu, a1);
+    a2 = __reduce_add_sync(0xffffffffu, a2);
+    am = __reduce_add_sync(0xffffffffu, am);
+    if (lane == 0) {
+        s_c1[wid] = a1;
+        s_c2[wid] = a2;
+        s_map[wid] = am;
+    }
+    __syncthreads();
+    uint32_t c1 = 0, c2 = 0, cmap = 0;
+    for (uint32_t w = 0; w < nw; ++w) {
+        if (w > wid) {
+            c1 += s_c1[w];
+            c2 += s_c2[w];
+        }
+        cmap += s_map[w];
+    }
+    unsigned long long walk = 0;
+    if (s1 > s0) {
+        for (uint32_t cs = (s1 - 1) & ~31u;; cs -= 32) {            // s0 is a multiple of 32
+            const uint32_t k = cs + lane;
+            const uint32_t e = k < s1 ? adj[ob + k] : 0u;
+            const uint32_t b1 = __ballot_sync(0xffffffffu, (e & 3u) == 1u);
+            const uint32_t b2 = __ballot_sync(0xffffffffu, (e & 3u) == 2u);
+            if (k < lv) {
+                const uint32_t u = e >> 2;
+                uint64_t lo = off[u] + up[u], hi = off[u + 1];
+                while (lo < hi) {
+                    const uint64_t mid = (lo + hi) >> 1;
+                    if ((adj[mid] >> 2) < (uint32_t)v) lo = mid + 1; else hi = mid;
+                }
+                const uint64_t idx = ub[u] + (lo - off[u] - up[u]);
+                rp[idx] = k;
+                vs[idx] = make_uint2(c1 + __popc(b1 & after), c2 + __popc(b2 & after));
+                walk += dv - k - 1;
+            } else if (k < s1) {
+                us[ub[v] + (k - lv)] = make_uint2(c1 + __popc(b1 & after), c2 + __popc(b2 & after));
+            }
+            c1 += __popc(b1);
+            c2 += __popc(b2);
+            if (cs == s0) break;
+        }
+    }
+    for (int o = 16; o; o >>= 1) walk += __shfl_xor_sync(0xffffffffu, walk, o);
+    if (lane == 0 && walk) atomicAdd(wk, walk);
+    if (threadIdx.x == 0) {
+        const unsigned long long m = min(lv, cmap);
+        const unsigned long long wm = m * cmap - m * (m + 1) / 2;
+        if (wm) atomicAdd(wk + 1, wm);
+    }
 }
 
 // upper pairs per vertex: deg - up
@@ -343,6 +426,12 @@ tc_status finish_graph(GraphStore& g, uint64_t E, int B, uint64_t* ukey, uint32_
                                                 g.ub.as<uint64_t>(), n, g.rp.as<uint32_t>(), g.vs.as<uint2>(), g.us.as<uint2>(),
                                                 stats.as<unsigned long long>() + 8);
             TC_LAUNCH("k_pair_tables");
+            // lists longer than kLongList: at most 2E / kLongList of them, the first ids
+            const uint64_t n_long = std::min<uint64_t>(n, 2ull * E / kLongList + 1);
+            k_pair_tables_long<<<(unsigned)n_long, kLongThreads, 0, st>>>(
+                g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(), g.ub.as<uint64_t>(), n,
+                g.rp.as<uint32_t>(), g.vs.as<uint2>(), g.us.as<uint2>(), stats.as<unsigned long long>() + 8);
+            TC_LAUNCH("k_pair_tables_long");
         }
     }
     unsigned long long hs[10];

@@ -743,60 +743,122 @@ __global__ void k_count_gt(const uint64_t* off, uint32_t n, uint32_t thr, uint32
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
 }
 
-// Items of the CTA-tier vertices u < u_end (plan.cuh), one warp per vertex; the learned
-// schedule fixes each vertex's item count from its predicted cost.
+// Items of the CTA-tier vertices u < u_end (plan.cuh), one warp per task: a block of at most
+// kMaxItemPairs upper pairs of one vertex.  The learned schedule fixes each vertex's item count
+// from its predicted cost.
 __device__ __forceinline__ double learned_items(const float* cost, uint64_t x, uint32_t item_work) {
     return cost ? fmax(1.0, ceil((double)cost[x] / (double)item_work)) : 0.0;
 }
 
-// W[x] = the work of vertex x's upper pairs, pu[pair] = each pair's (by table index, pairs of
-// vertices x < u_end); total[0] += the sum (sizes the items when the options leave item_work
-// to the graph).
-__global__ void k_plan_work(GraphDev g, uint32_t u_end, uint32_t chunk, int algo, unsigned long long* W, uint32_t* pu,
-                            unsigned long long* total) {
+// tcnt[x] = the tasks of vertex x: its upper pairs in blocks of kMaxItemPairs
+__global__ void k_task_count(const uint64_t* __restrict__ off, const uint32_t* __restrict__ up, uint32_t u_end,
+                             uint32_t* tcnt) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < u_end; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t upper = (uint32_t)(off[x + 1] - off[x]) - up[x];
+        tcnt[x] = (upper + kMaxItemPairs - 1) / kMaxItemPairs;
+    }
+}
+
+// owner[t] = the vertex of task t (tasks numbered by vertex, then block)
+__global__ void k_task_owner(const uint32_t* __restrict__ tbase, const uint32_t* __restrict__ tcnt, uint32_t u_end,
+                             uint32_t* owner) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < u_end; x += (uint64_t)gridDim.x * blockDim.x)
+        for (uint32_t b = 0, t = tbase[x]; b < tcnt[x]; ++b) owner[t + b] = (uint32_t)x;
+}
+
+// The pair range [j0, j1) of task t, owned by vertex x.
+struct Task {
+    uint32_t x, b, j0, j1;
+};
+__device__ __forceinline__ Task task_of(const GraphDev& g, const uint32_t* owner, const uint32_t* tbase, uint64_t t) {
+    Task k;
+    k.x = owner[t];
+    k.b = (uint32_t)(t - tbase[k.x]);
+    const uint32_t du = (uint32_t)(g.off[k.x + 1] - g.off[k.x]);
+    k.j0 = g.up[k.x] + k.b * kMaxItemPairs;
+    k.j1 = du - k.j0 > kMaxItemPairs ? k.j0 + kMaxItemPairs : du;
+    return k;
+}
+
+// pu[pair] = each pair's work (by table index), tw[t] = task t's total; total[0] += the sum
+// (sizes the items when the options leave item_work to the graph).
+__global__ void k_plan_work(GraphDev g, const uint32_t* __restrict__ owner, const uint32_t* __restrict__ tbase,
+                            const uint32_t* __restrict__ n_tasks, uint32_t chunk, int algo, unsigned long long* tw,
+                            uint32_t* pu, unsigned long long* total) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t T = *n_tasks;
     unsigned long long sum = 0;
-    for (uint64_t x = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; x < u_end; x += warps) {
-        const uint64_t ubase = g.off[x];
-        const uint32_t du = (uint32_t)(g.off[x + 1] - ubase), upx = g.up[x];
+    for (uint64_t t = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; t < T; t += warps) {
+        const Task k = task_of(g, owner, tbase, t);
+        const uint64_t ubase = g.off[k.x];
+        const uint32_t du = (uint32_t)(g.off[k.x + 1] - ubase), upx = g.up[k.x];
         const uint32_t chunks = (du + chunk - 1) / chunk;
-        const uint64_t tb = g.ub[x] - upx;
+        const uint64_t tb = g.ub[k.x] - upx;
         unsigned long long w = 0;
-        for (uint32_t j = upx + lane; j < du; j += 32) {
-            const uint64_t c = pair_units(g, (uint32_t)x, ubase, du, upx, j, chunks, algo);
-            pu[tb + j] = c < 0xffffffffull ? (uint32_t)c : 0xffffffffu;
-            w += c;
+        for (uint32_t j = k.j0 + lane; j < k.j1; j += 32) {
+            const uint64_t c = pair_units(g, k.x, ubase, du, upx, j, chunks, algo);
+            const uint32_t c32 = c < 0xffffffffull ? (uint32_t)c : 0xffffffffu;
+            pu[tb + j] = c32;
+            w += c32;
         }
         for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
         sum += w;
-        if (lane == 0) W[x] = w;
+        if (lane == 0) tw[t] = w;
     }
     if (lane == 0 && sum) atomicAdd(total, sum);
 }
 
-__global__ void k_plan_count(GraphDev g, uint32_t u_end, uint32_t item_work, const float* cost,
-                             const unsigned long long* W, const uint32_t* pu, uint32_t* cnt) {
-    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t x = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; x < u_end; x += warps) {
-        const uint64_t tb = g.ub[x] - g.up[x];
-        const uint32_t c = plan_vertex(g, (uint32_t)x, item_work, learned_items(cost, x, item_work), W[x],
-                                       [&](uint32_t j) { return (unsigned long long)pu[tb + j]; },
-                                       [](uint32_t, uint32_t) {});
-        if ((threadIdx.x & 31) == 0) cnt[x] = c;
+// One warp: the work of vertex x's tasks before task b (pre) and in all (W).
+__device__ __forceinline__ void task_frame(const uint32_t* tbase, const uint32_t* tcnt, const unsigned long long* tw,
+                                           const Task& k, unsigned long long& pre, unsigned long long& W) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t base = tbase[k.x], nt = tcnt[k.x];
+    unsigned long long a = 0, p = 0;
+    for (uint32_t i = lane; i < nt; i += 32) {
+        const unsigned long long v = tw[base + i];
+        a += v;
+        if (i < k.b) p += v;
     }
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        p += __shfl_xor_sync(0xffffffffu, p, o);
+    }
+    pre = p;
+    W = a;
 }
 
-__global__ void k_plan_emit(GraphDev g, uint32_t u_end, uint32_t item_work, const float* cost,
-                            const unsigned long long* W, const uint32_t* pu, const uint32_t* pos, Item* items) {
+struct PlanArgs {
+    const uint32_t *owner, *tbase, *tcnt, *n_tasks, *pu;
+    const unsigned long long *tw, *total;
+    const float* cost;
+    uint32_t item_work;   // 0: adaptive_item_work(total, grid)
+    uint32_t grid;
+};
+
+// cnt[t] = the items of task t (with emit: the items themselves, at items + pos[t])
+template <bool EMIT>
+__global__ void k_plan_items(GraphDev g, PlanArgs a, const uint32_t* __restrict__ pos, uint32_t* cnt, Item* items) {
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t x = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; x < u_end; x += warps) {
-        Item* out = items + pos[x];
-        const uint64_t tb = g.ub[x] - g.up[x];
-        const uint32_t c = plan_vertex(g, (uint32_t)x, item_work, learned_items(cost, x, item_work), W[x],
-                                       [&](uint32_t j) { return (unsigned long long)pu[tb + j]; },
-                                       [&](uint32_t j, uint32_t rank) { out[rank] = Item{(uint32_t)x, j, 0u, 0u}; });
-        plan_vertex_ends(out, c, (uint32_t)(g.off[x + 1] - g.off[x]));
+    const uint32_t T = *a.n_tasks;
+    const uint32_t iw = a.item_work ? a.item_work : adaptive_item_work(*a.total, a.grid);
+    for (uint64_t t = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; t < T; t += warps) {
+        const Task k = task_of(g, a.owner, a.tbase, t);
+        unsigned long long pre, W;
+        task_frame(a.tbase, a.tcnt, a.tw, k, pre, W);
+        const float S = plan_items(W, iw, learned_items(a.cost, k.x, iw));
+        const uint64_t tb = g.ub[k.x] - g.up[k.x];
+        const uint32_t* pu = a.pu;
+        auto units = [&](uint32_t j) { return (unsigned long long)pu[tb + j]; };
+        if (EMIT) {
+            Item* out = items + pos[t];
+            const uint32_t c = plan_block(k.j0, k.j1, pre, W, S, units,
+                                          [&](uint32_t j, uint32_t rank) { out[rank] = Item{k.x, j, 0u, 0u}; });
+            plan_ends(out, c, k.j1);
+        } else {
+            const uint32_t c = plan_block(k.j0, k.j1, pre, W, S, units, [](uint32_t, uint32_t) {});
+            if ((threadIdx.x & 31) == 0) cnt[t] = c;
+        }
     }
 }
 
@@ -886,34 +948,53 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out) {
     p.warp_end = g.n_active;
     p.n_items = 0;
     if (u_end) {
-        DevBuf cnt, pos, tot, wv, wt, pu;
-        TC_TRY(cnt.alloc(sizeof(uint32_t) * u_end, st));
-        TC_TRY(pos.alloc(sizeof(uint32_t) * u_end, st));
-        TC_TRY(tot.alloc(sizeof(uint32_t), st));
-        TC_TRY(wv.alloc(sizeof(unsigned long long) * u_end, st));
+        // tasks: blocks of at most kMaxItemPairs upper pairs, at most u_end + e_sym / kMaxItemPairs
+        const uint64_t tmax = (uint64_t)u_end + g.e_sym / kMaxItemPairs + 1;
+        if (tmax >= (1ull << 32)) return fail(TC_ERR_RANGE, "too many plan tasks");
+        DevBuf tcnt, tbase, ntask, owner, tw, wt, pu, cnt, pos, tot;
+        TC_TRY(tcnt.alloc(sizeof(uint32_t) * u_end, st));
+        TC_TRY(tbase.alloc(sizeof(uint32_t) * u_end, st));
+        TC_TRY(ntask.alloc(sizeof(uint32_t), st));
+        TC_TRY(owner.alloc(sizeof(uint32_t) * tmax, st));
+        TC_TRY(tw.alloc(sizeof(unsigned long long) * tmax, st));
         TC_TRY(wt.alloc(sizeof(unsigned long long), st));
         TC_TRY(pu.alloc(sizeof(uint32_t) * (g.e_sym ? g.e_sym : 1), st));   // pair units by table index
+        TC_TRY(cnt.alloc(sizeof(uint32_t) * tmax, st));
+        TC_TRY(pos.alloc(sizeof(uint32_t) * tmax, st));
+        TC_TRY(tot.alloc(sizeof(uint32_t), st));
         TC_CUDA(cudaMemsetAsync(wt.p, 0, sizeof(unsigned long long), st));
-        const float* cost = (o.schedule == TC_SCHED_LEARNED) ? g.cost.as<float>() : nullptr;
-        const unsigned pgrid = grid_for((uint64_t)u_end * 32, 256, 8192);
-        k_plan_work<<<pgrid, 256, 0, st>>>(gd, u_end, o.chunk, (int)o.algo, wv.as<unsigned long long>(), pu.as<uint32_t>(),
+        TC_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(uint32_t) * tmax, st));
+        const unsigned vgrid = grid_for(u_end, 256, 4096);
+        k_task_count<<<vgrid, 256, 0, st>>>(gd.off, gd.up, u_end, tcnt.as<uint32_t>());
+        TC_LAUNCH("k_task_count");
+        TC_TRY(scan_u32(tcnt.as<uint32_t>(), tbase.as<uint32_t>(), u_end, ntask.as<uint32_t>(), st));
+        k_task_owner<<<vgrid, 256, 0, st>>>(tbase.as<uint32_t>(), tcnt.as<uint32_t>(), u_end, owner.as<uint32_t>());
+        TC_LAUNCH("k_task_owner");
+        const unsigned tgrid = grid_for(tmax * 32, 256, 8192);
+        k_plan_work<<<tgrid, 256, 0, st>>>(gd, owner.as<uint32_t>(), tbase.as<uint32_t>(), ntask.as<uint32_t>(), o.chunk,
+                                           (int)o.algo, tw.as<unsigned long long>(), pu.as<uint32_t>(),
                                            wt.as<unsigned long long>());
         TC_LAUNCH("k_plan_work");
-        unsigned long long total_units = 0;
-        TC_CUDA(cudaMemcpyAsync(&total_units, wt.p, sizeof(total_units), cudaMemcpyDeviceToHost, st));
-        TC_CUDA(cudaStreamSynchronize(st));
-        const uint32_t iw = o.item_work ? o.item_work : adaptive_item_work(total_units, (unsigned)census_grid(o));
-        k_plan_count<<<pgrid, 256, 0, st>>>(gd, u_end, iw, cost, wv.as<unsigned long long>(), pu.as<uint32_t>(),
-                                            cnt.as<uint32_t>());
-        TC_LAUNCH("k_plan_count");
-        TC_TRY(scan_u32(cnt.as<uint32_t>(), pos.as<uint32_t>(), u_end, tot.as<uint32_t>(), st));
+        PlanArgs pa;
+        pa.owner = owner.as<uint32_t>();
+        pa.tbase = tbase.as<uint32_t>();
+        pa.tcnt = tcnt.as<uint32_t>();
+        pa.n_tasks = ntask.as<uint32_t>();
+        pa.pu = pu.as<uint32_t>();
+        pa.tw = tw.as<unsigned long long>();
+        pa.total = wt.as<unsigned long long>();
+        pa.cost = (o.schedule == TC_SCHED_LEARNED) ? g.cost.as<float>() : nullptr;
+        pa.item_work = o.item_work;
+        pa.grid = (uint32_t)census_grid(o);
+        k_plan_items<false><<<tgrid, 256, 0, st>>>(gd, pa, nullptr, cnt.as<uint32_t>(), nullptr);
+        TC_LAUNCH("k_plan_items (count)");
+        TC_TRY(scan_u32(cnt.as<uint32_t>(), pos.as<uint32_t>(), tmax, tot.as<uint32_t>(), st));
         TC_CUDA(cudaMemcpyAsync(&p.n_items, tot.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         TC_CUDA(cudaStreamSynchronize(st));
         TC_TRY(p.items.alloc_persistent(sizeof(Item) * (p.n_items ? p.n_items : 1)));
         if (p.n_items) {
-            k_plan_emit<<<pgrid, 256, 0, st>>>(gd, u_end, iw, cost, wv.as<unsigned long long>(), pu.as<uint32_t>(),
-                                               pos.as<uint32_t>(), p.items.as<Item>());
-            TC_LAUNCH("k_plan_emit");
+            k_plan_items<true><<<tgrid, 256, 0, st>>>(gd, pa, pos.as<uint32_t>(), nullptr, p.items.as<Item>());
+            TC_LAUNCH("k_plan_items (emit)");
         }
         TC_CUDA(cudaStreamSynchronize(st));
     }

@@ -29,7 +29,7 @@ struct Opts {
 tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out);
 // Work units per CTA item when none is set: about four items per CTA of the launch, so a large
 // census re-stages hub lists rarely and a small one still spreads over every SM.
-inline uint32_t adaptive_item_work(unsigned long long total_units, unsigned grid) {
+__host__ __device__ inline uint32_t adaptive_item_work(unsigned long long total_units, unsigned grid) {
     unsigned long long w = total_units / (4ull * (grid ? grid : 1u));
     if (w < (1ull << 14)) w = 1ull << 14;
     if (w > (1ull << 22)) w = 1ull << 22;
