@@ -2,6 +2,7 @@
 // the 128-bit null count of Fig. 5 steps 3-5.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "graph.cuh"
@@ -29,16 +30,67 @@ tc_status cuda_fail(cudaError_t e, const char* what) {
     return TC_ERR_CUDA;
 }
 
-tc_status DevBuf::alloc(size_t b, cudaStream_t s) {
-    release();
-    if (b == 0) b = 16;
-    cudaError_t e = cudaMallocAsync(&p, b, s);
+namespace {
+
+// The library's own stream-ordered memory pool on each device.  Freed blocks stay in it, up to
+// a quarter of the device's memory, for the next graph or call: the driver's default pool gives
+// them back at every synchronisation, so each build paid again for mapping its temporaries.
+// Persistent buffers come from the same pool on a stream of their own that is synchronised
+// at once, so they are valid on every stream when alloc_persistent returns.
+struct DevicePool {
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t st = nullptr;
+};
+std::mutex g_pool_mu;
+DevicePool g_pools[64];
+
+tc_status device_pool(DevicePool* out) {
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TC_ERR_CUDA, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    DevicePool& d = g_pools[dev];
+    if (!d.pool) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        size_t fr = 0, total = 0;
+        TC_CUDA(cudaMemGetInfo(&fr, &total));
+        cudaMemPool_t pool = nullptr;
+        TC_CUDA(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = total / 4;
+        TC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        cudaStream_t st = nullptr;
+        TC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        d.pool = pool;
+        d.st = st;
+    }
+    *out = d;
+    return TC_OK;
+}
+
+tc_status pool_alloc(void** p, size_t b, cudaStream_t s, const DevicePool& d) {
+    cudaError_t e = cudaMallocFromPoolAsync(p, b, d.pool, s);
     if (e != cudaSuccess) {
-        p = nullptr;
+        *p = nullptr;
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? TC_ERR_OOM : TC_ERR_CUDA,
                     std::string("device allocation of ") + std::to_string(b) + " bytes: " + cudaGetErrorString(e));
     }
+    return TC_OK;
+}
+
+}  // namespace
+
+tc_status DevBuf::alloc(size_t b, cudaStream_t s) {
+    release();
+    if (b == 0) b = 16;
+    DevicePool d;
+    TC_TRY(device_pool(&d));
+    TC_TRY(pool_alloc(&p, b, s, d));
     bytes = b;
     st = s;
     async = true;
@@ -48,22 +100,26 @@ tc_status DevBuf::alloc(size_t b, cudaStream_t s) {
 tc_status DevBuf::alloc_persistent(size_t b) {
     release();
     if (b == 0) b = 16;
-    cudaError_t e = cudaMalloc(&p, b);
+    DevicePool d;
+    TC_TRY(device_pool(&d));
+    TC_TRY(pool_alloc(&p, b, d.st, d));
+    const cudaError_t e = cudaStreamSynchronize(d.st);
     if (e != cudaSuccess) {
+        cudaFreeAsync(p, d.st);
         p = nullptr;
-        cudaGetLastError();
-        return fail(e == cudaErrorMemoryAllocation ? TC_ERR_OOM : TC_ERR_CUDA,
-                    std::string("device allocation of ") + std::to_string(b) + " bytes: " + cudaGetErrorString(e));
+        return cuda_fail(e, "device allocation");
     }
     bytes = b;
+    st = d.st;
     async = false;
     return TC_OK;
 }
 
 void DevBuf::release() {
     if (p) {
-        if (async) cudaFreeAsync(p, st);
-        else cudaFree(p);
+        // a persistent buffer may be in use on any stream: like cudaFree, wait for the device
+        if (!async) cudaDeviceSynchronize();
+        cudaFreeAsync(p, st);
     }
     p = nullptr;
     bytes = 0;
