@@ -16,8 +16,10 @@
  *   - Return a tc_status; TC_OK is 0.  On failure nothing is written to the outputs, and
  *     tc_last_error() returns a message for the calling thread.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
- *   - Device memory the library needs for a graph is allocated stream-ordered on the
- *     graph's creation stream and owned by the tc_graph until tc_graph_destroy.
+ *   - Device memory comes from the library's own stream-ordered pool on each device; freed
+ *     blocks stay in the pool (up to a quarter of the device's memory) for later calls.
+ *     A graph's buffers are owned by the tc_graph until tc_graph_destroy, which first waits
+ *     for the device (as cudaFree does); temporaries are released in stream order.
  *   - The caller keeps ownership of every buffer it passes; inputs are copied.
  *   - Vertex ids are uint32 and must be < n; n must be <= 2^30 because each stored id
  *     carries two direction bits (Sec. 6).
