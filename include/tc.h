@@ -71,7 +71,8 @@ typedef struct {
     uint32_t schedule;        /* tc_schedule, default TC_SCHED_PLAIN */
     uint32_t warp_max_deg;    /* vertices u with deg <= this run one warp per u (default 64) */
     uint32_t chunk_entries;   /* neighbour entries of u staged per CTA: power of 2 in [512, 16384],
-                                 at most 8192 for TC_ALGO_SUFFIX (default 4096) */
+                                 at most 8192 for TC_ALGO_SUFFIX (default 2048 for TC_ALGO_SUFFIX,
+                                 4096 for TC_ALGO_UNION) */
     uint32_t item_work;       /* work per CTA item, in list entries walked plus pair overheads
                                  (0 = sized to the graph: about four items per CTA, 2^14 to 2^22) */
     uint32_t ctas_per_sm;     /* persistent CTAs per SM (default 3) */

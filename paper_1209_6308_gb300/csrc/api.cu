@@ -150,7 +150,12 @@ tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out) {
     Opts o = merge_opts(in, base);
     if (o.algo > TC_ALGO_SUFFIX) return fail(TC_ERR_ARG, "unknown algo");
     if (o.schedule > TC_SCHED_LEARNED) return fail(TC_ERR_ARG, "unknown schedule");
-    if (!o.chunk) o.chunk = 4096;
+    // the suffix form's hash takes 4 slots per entry, the union walk's 2 plus the sorted copy:
+    // both fill about 70 KB of shared memory, three CTAs per SM
+    if (!o.chunk) {
+        o.chunk = o.algo == TC_ALGO_SUFFIX ? 2048u : 4096u;
+        o.chunk_auto = true;
+    }
     if (!o.ctas_per_sm) o.ctas_per_sm = 3;
     const uint32_t max_chunk = o.algo == TC_ALGO_SUFFIX ? 8192u : 16384u;   // shared-memory hash sizes
     if (o.chunk < 512 || o.chunk > max_chunk || (o.chunk & (o.chunk - 1)))
@@ -354,6 +359,7 @@ tc_status tc_census_async(tc_graph* g, void* stream, const tc_options* opt, uint
     TC_TRY(resolve_opts(opt, &g->s.opts, &o));
     std::unique_lock<std::mutex> lk(g->s.busy, std::try_to_lock);
     if (!lk.owns_lock()) return fail(TC_ERR_BUSY, "graph is in use by another call");
+    census_fit_chunk(g->s, o);
     Plan* p = nullptr;
     TC_TRY(get_plan(g->s, o, st, &p));
     TC_CUDA(cudaMemsetAsync(d_out16, 0, sizeof(uint64_t) * 16, st));
@@ -368,6 +374,7 @@ tc_status tc_census_profile(tc_graph* g, void* stream, const tc_options* opt, ui
     TC_TRY(resolve_opts(opt, &g->s.opts, &o));
     std::unique_lock<std::mutex> lk(g->s.busy, std::try_to_lock);
     if (!lk.owns_lock()) return fail(TC_ERR_BUSY, "graph is in use by another call");
+    census_fit_chunk(g->s, o);
     Plan* p = nullptr;
     TC_TRY(get_plan(g->s, o, st, &p));
     TC_CUDA(cudaMemsetAsync(d_out16, 0, sizeof(uint64_t) * 16, st));
@@ -388,6 +395,7 @@ tc_status tc_census_opts(tc_graph* g, void* stream, const tc_options* opt, tc_u1
     TC_TRY(resolve_opts(opt, &g->s.opts, &o));
     std::unique_lock<std::mutex> lk(g->s.busy, std::try_to_lock);
     if (!lk.owns_lock()) return fail(TC_ERR_BUSY, "graph is in use by another call");
+    census_fit_chunk(g->s, o);
     Plan* p = nullptr;
     TC_TRY(get_plan(g->s, o, st, &p));
     TC_CUDA(cudaMemsetAsync(g->s.acc.p, 0, sizeof(unsigned long long) * 16, st));

@@ -9,8 +9,8 @@
 namespace tc {
 
 // Census options.  chunk and ctas_per_sm may be 0 (= automatic) until finalised for the
-// chosen kernel family: the suffix form keeps only a hash in shared memory, so it takes
-// twice the chunk at two CTAs per SM; the union walk also keeps the sorted chunk.
+// chosen kernel family: the suffix form keeps a hash of 4 slots per staged entry (2048
+// entries by default), the union walk one of 2 slots plus the sorted chunk (4096).
 struct Opts {
     uint32_t algo = TC_ALGO_UNION;
     uint32_t schedule = TC_SCHED_PLAIN;
@@ -19,6 +19,7 @@ struct Opts {
     uint32_t item_work = 0;   // 0: sized to the graph (adaptive_item_work)
     uint32_t ctas_per_sm = 0;
     uint32_t map_mode = 0;    // 0 auto, 1 always, 2 never (single-graph census with tables)
+    bool chunk_auto = false;  // chunk was left to the library (census_fit_chunk may widen it)
     bool operator==(const Opts& o) const {
         return algo == o.algo && schedule == o.schedule && warp_max_deg == o.warp_max_deg && chunk == o.chunk &&
                item_work == o.item_work && ctas_per_sm == o.ctas_per_sm && map_mode == o.map_mode;
@@ -108,6 +109,10 @@ tc_status build_from_csr(GraphStore& g, const uint64_t* d_off, const uint32_t* d
 // caller zeroes; index 0 is never touched).  No host synchronisation, no allocation once
 // the plan for `o` exists (get_plan allocates it on first use).
 tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out);
+// The single-graph census's form (map or not) and, for an automatic chunk, its size: call
+// before get_plan, whose items depend on the chunk.
+bool census_map(const GraphStore& g, const Opts& o);
+void census_fit_chunk(const GraphStore& g, Opts& o);
 // d_vcost (optional, [n] uint64, caller-zeroed) receives the SM cycles spent per vertex u;
 // d_phase (optional, [3 * CTAs] uint64) the globaltimer at start, end of items, end per CTA.
 tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16,

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 ALGOS = [{"algo": 0}, {"algo": 1}]
 TIERS = [
-    {},                                                       # defaults: warp <= 64, chunk 4096
+    {},                                                       # defaults: warp <= 64, chunk 2048 / 4096
     {"warp_max_deg": 8, "chunk_entries": 512, "item_work": 2048},   # tiny chunks: hubs split
     {"warp_max_deg": 64, "chunk_entries": 8192, "item_work": 1 << 22, "ctas_per_sm": 1},
     {"map_mode": 2},                                          # no id map: every entry hashed
