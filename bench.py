@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -214,12 +215,20 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def census_code_hash(text: str) -> str:
+    """First 16 hex digits of the SHA-256 of census.cu's code: comments, trailing blanks and
+    empty lines removed, so that edits of comments alone keep a capture's counters valid."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    code = "\n".join(ln for ln in lines if ln.strip())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
+
+
 def stored_traffic():
-    """Per-launch DRAM bytes from the committed ncu summary, if taken on this census.cu."""
+    """Per-launch DRAM bytes from the committed ncu summary, if taken on this census.cu code."""
     try:
         kv = dict(line.split(":", 1) for line in open(TRAFFIC_FILE) if ":" in line)
-        src_hash = hashlib.sha256(open(CENSUS_SRC, "rb").read()).hexdigest()[:16]
-        if kv.get("census_cu_sha256_16", "").strip() == src_hash:
+        if kv.get("census_code_sha256_16", "").strip() == census_code_hash(open(CENSUS_SRC).read()):
             return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         pass

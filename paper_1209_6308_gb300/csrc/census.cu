@@ -2,30 +2,30 @@
 //
 // Vertices are in descending-degree ids, so for every connected pair (u, v) with u < v
 // (step 2.1) u is the endpoint of larger degree.  For each pair the kernel accounts for every
-// third vertex w of S = N[u] u N[v] \ {u, v} (step 2.1.1, the union of Sec. 6 / Fig. 8) in
-// two sweeps that together visit S exactly once:
-//   - the v side: each w in N[v] is looked up in N[u] (staged in shared memory as a sorted
-//     array plus an open-addressing hash).  A common w counts toward |N[u] n N[v]|; a common
-//     w > v is a connected triad with both u-w and v-w links; a w in N[v] only, with w > u,
-//     is a connected triad through v alone (the canonical rule of step 2.1.4).
-//   - the u side: the w in N[u] past v (the rest of S that the canonical rule keeps: w > v)
-//     are classified as triads through u alone; the common ones among them were already
-//     counted with both links by the v side, which therefore also removes their u-only count.
-//   TC_ALGO_UNION walks the u side one w at a time and looks each class up in the 64-entry
-//     tricode table (step 2.1.4.1).
-//   TC_ALGO_SUFFIX gets the same u-side counts per direction class from prefix counts of the
-//     staged list: for a w reached from u alone the class depends only on dir(u,v) and
-//     dir(u,w), so the three counts, each sent through the same table, give the same census.
+// third vertex w of S = N[u] u N[v] \ {u, v} (step 2.1.1, the union of Sec. 6 / Fig. 8) once:
+//   - the v side: entries w of N[v] are looked up in N[u], staged in shared memory (a direct
+//     map of two direction bits per id for the lowest ids, an open-addressing hash for the
+//     rest).  A common w > v is a triad with both u-w and v-w links (classified through the
+//     64-entry tricode table, step 2.1.4.1); a w in N[v] only, with w > u, is a triad through
+//     v alone (the canonical rule of step 2.1.4).  With the per upper pair tables of the graph
+//     the walk starts past u, and the triads through v alone are the table's direction-class
+//     counts of N[v] past u minus the common neighbours found; the common neighbours below u
+//     reach the pair's dyadic count as credits from the pairs (w, u) that found its triangle.
+//   - the u side: the w in N[u] past v (the rest of S that the canonical rule keeps) are
+//     triads through u alone, whose class depends only on dir(u,v) and dir(u,w).
+//     TC_ALGO_SUFFIX takes their counts per direction class (from the per-pair table, or from
+//     prefix counts of the staged chunk), less the common ones the v side already counted;
+//     TC_ALGO_UNION walks them one by one.
 // The dyadic triads of the pair (steps 2.1.2-2.1.3) add n - |S| - 2 = n - d_u - d_v + |common|
-// to 012 or 102.  Counts go to per-thread shared-memory histograms (class-major, one column
-// per thread: no bank conflicts), per-warp 64-bit accumulators, and at the end 16 64-bit
-// atomics per CTA (the private census vectors of Sec. 6).
+// to 012 or 102.  Counts go to per-lane packed 8-bit class counters, flushed by warp
+// reductions into per-lane 64-bit class totals, and at the end to 16 64-bit atomics per CTA
+// (the private census vectors of Sec. 6).
 //
 // Work decomposition ("manhattan collapse" of Sec. 7): vertices with deg > warp_max_deg
-// become CTA items (u, range of pairs), sized by the schedule.  N[u] is staged one chunk at
-// a time; when a hub's list takes several chunks, each pair keeps a cursor into its sorted
-// N[v] and every chunk consumes the N[v] entries below the next chunk's first id, so each
-// N[v] entry is read once per pair with no search.  Vertices with smaller degree are
+// become CTA items (u, range of pairs), cut by exact pair work (plan.cuh).  N[u] is staged
+// one chunk at a time; when a hub's list takes several chunks, each pair keeps a cursor into
+// its sorted N[v] and every chunk consumes the N[v] entries below the next chunk's first id,
+// so each N[v] entry is read once per pair with no search.  Vertices with smaller degree are
 // handled one warp per vertex after the items run out, in the same persistent launch.
 #include <atomic>
 #include <cstring>
@@ -52,7 +52,7 @@ constexpr uint32_t kTrip = 32u * TC_UNROLL;  // entries of N[v] per warp trip
 // make up most of the N[v] entries walked) sit in a direct map of two direction bits per id;
 // the rest in the open-addressing hash.
 // MAP selects the map; without it (graphs whose walks meet mostly ids past the map's range)
-// every entry goes to a hash of 4x the chunk (2x for the union walk, beside its sorted copy).
+// every entry of the chunk goes to the hash.
 template <int ALGO, bool MAP> constexpr uint32_t map_ids() {
     return MAP ? (ALGO == TC_ALGO_UNION ? kMapIdsUnion : kMapIdsSuffix) : 0u;
 }

@@ -80,3 +80,16 @@ def test_reference_arm_on_other_ranks_exits_without_work(monkeypatch):
     monkeypatch.setattr(bench, "workload", lambda: called.append(1))
     assert bench.run_reference(bench.parse()) == 0
     assert not called
+
+
+def test_census_code_hash_ignores_comments_only():
+    """The stored DRAM traffic stays valid across comment edits of census.cu, not code edits."""
+    import bench
+    src = "int a = 1; // one\n/* block\n comment */\n\nint b = 2;\n"
+    same = "// header\nint a = 1;\n\nint b = 2;   \n"
+    other = "int a = 1;\nint b = 3;\n"
+    assert bench.census_code_hash(src) == bench.census_code_hash(same)
+    assert bench.census_code_hash(src) != bench.census_code_hash(other)
+    with open(bench.TRAFFIC_FILE) as f:
+        kv = dict(line.split(":", 1) for line in f if ":" in line and not line.startswith("#"))
+    assert "census_code_sha256_16" in kv and float(kv["dram_bytes_per_launch"]) > 0
