@@ -52,6 +52,8 @@ def _load():
         lib.or_census_bm_parallel.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p, ctypes.c_int]
         lib.or_census_brute.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p]
         lib.or_invariants.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p]
+        lib.or_census64_brute.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p]
+        lib.or_census64.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p]
         lib.or_graph_new.restype = ctypes.c_void_p
         lib.or_graph_new.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p]
         lib.or_graph_free.argtypes = [ctypes.c_void_p]
@@ -120,6 +122,36 @@ def census_brute(n: int, src, dst):
     if rc != 0:
         raise ValueError(f"brute-force census refused (code {rc})")
     return _u128(out, 16)
+
+
+def census64_brute(n: int, src, dst):
+    """64-state census by definition (n <= 4096): the state of every a<b<c over the roles
+    (u, v, w) = (a, b, c), tricode bits 1 v->u, 2 u->v, 4 v->w, 8 w->v, 16 u->w, 32 w->u."""
+    s, d, ps, pd = _arcs(src, dst)
+    out = np.zeros(128, dtype=np.uint64)
+    rc = _load().or_census64_brute(n, len(s), ps, pd, _p64(out))
+    if rc != 0:
+        raise ValueError(f"brute-force 64-state census refused (code {rc})")
+    return _u128(out, 64)
+
+
+def census64(n: int, src, dst):
+    """64-state census per linked pair (first-linked-pair rule, range counts, null by
+    subtraction): the same states as census64_brute, for any n."""
+    s, d, ps, pd = _arcs(src, dst)
+    out = np.zeros(128, dtype=np.uint64)
+    if _load().or_census64(n, len(s), ps, pd, _p64(out)) != 0:
+        raise ValueError("vertex id out of range")
+    return _u128(out, 64)
+
+
+def fold64(c64) -> list:
+    """The 16-class census of a 64-state census (Sec. 3: isomorphic states merged)."""
+    t = table_rules()
+    out = [0] * 16
+    for code, k in enumerate(c64):
+        out[int(t[code])] += int(k)
+    return out
 
 
 def invariants(n: int, src, dst) -> dict:

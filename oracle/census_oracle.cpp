@@ -18,6 +18,22 @@
 //                         (dyad totals, 2-stars, 2-paths, triangles); the tests combine
 //                         them with per-class constants.
 //
+// The 64-state census (Sec. 3, Fig. 2: the labelled triad states before the fold to 16
+// classes), two more independent routes:
+//   4. or_census64_brute - every a<b<c, its state read over the roles (a, b, c).  Small n.
+//   5. or_census64       - per linked pair (a, b), a<b: the merge of N(a) and N(b) gives
+//                          every third vertex linked to a or b; such a triad is counted at
+//                          its first linked pair in the order (x,y) < (x,z) < (y,z) of its
+//                          sorted vertices x<y<z.  Third vertices linked to neither are
+//                          counted per position (below a, between, above b) as the range's
+//                          size less the merged vertices in it; the null state by
+//                          subtraction.  Neither Fig. 5's third-vertex rule nor anything of
+//                          the GPU method is used.
+//   Reading: the paper names 64 states of a triad's three actors without fixing which actor
+//   takes which role; the state here orders them by vertex id, the caller's labels (roles
+//   u = smallest, v = middle, w = largest id, bits as the tricode).  Folded through the
+//   16-class table, the 64-state census gives the 16-class census.
+//
 // The tricode -> class table is derived twice, by different methods, and the tests check
 // that the two agree: or_table_rules (mutual/asymmetric/null dyad counts plus direction
 // tests) and or_table_canonical (minimum code over the 6 vertex permutations matched
@@ -275,9 +291,106 @@ void bm_finish(uint64_t n, u128 census[16]) {
     census[T003] = choose3(n) - sum;                             // step 5
 }
 
+// ------------------------------------------------------------------ 64-state census
+// The state of {a<b<c} over the roles (u, v, w) = (a, b, c), bits as the tricode.
+int state_of(bool ab, bool ba, bool bc, bool cb, bool ac, bool ca) {
+    return (ba ? 1 : 0) | (ab ? 2 : 0) | (bc ? 4 : 0) | (cb ? 8 : 0) | (ac ? 16 : 0) | (ca ? 32 : 0);
+}
+
+void store64(const u128 c[64], uint64_t* out) {
+    for (int t = 0; t < 64; ++t) { out[2 * t] = (uint64_t)c[t]; out[2 * t + 1] = (uint64_t)(c[t] >> 64); }
+}
+
+// Direction of a link seen from one end x: out = x->other, in = other->x.
+struct Link { bool out, in; };
+
 }  // namespace
 
 extern "C" {
+
+// Route 4: the O(n^3) definition of the 64-state census.
+int or_census64_brute(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst, uint64_t* out) {
+    if (n > 4096) return -2;
+    std::vector<uint8_t> adj((size_t)n * n, 0);
+    for (uint64_t i = 0; i < m; ++i) {
+        if (src[i] >= n || dst[i] >= n) return -1;
+        if (src[i] != dst[i]) adj[(size_t)src[i] * n + dst[i]] = 1;
+    }
+    auto A = [&](uint32_t x, uint32_t y) { return adj[(size_t)x * n + y] != 0; };
+    std::vector<u128> census(64, 0);
+    for (uint32_t a = 0; a < n; ++a)
+        for (uint32_t b = a + 1; b < n; ++b)
+            for (uint32_t c = b + 1; c < n; ++c)
+                census[state_of(A(a, b), A(b, a), A(b, c), A(c, b), A(a, c), A(c, a))] += 1;
+    store64(census.data(), out);
+    return 0;
+}
+
+// Route 5: per linked pair, first-linked-pair rule for connected triads, range counts for
+// the triads whose only link is the pair, null state by subtraction.
+int or_census64(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst, uint64_t* out) {
+    Digraph g;
+    if (!build_digraph(n, m, src, dst, g)) return -1;
+    std::vector<u128> census(64, 0);
+    for (uint32_t a = 0; a < n; ++a) {
+        for (const Tagged& tb : g.N[a]) {
+            const uint32_t b = tb.id;
+            if (b <= a) continue;
+            const bool ab = tb.out, ba = tb.in;   // a->b, b->a
+            // merge N(a) and N(b) without a and b: every third vertex linked to a or b
+            const auto& Na = g.N[a];
+            const auto& Nb = g.N[b];
+            size_t i = 0, j = 0;
+            uint64_t below = 0, between = 0, above = 0;   // merged vertices per range
+            while (i < Na.size() || j < Nb.size()) {
+                uint32_t c;
+                Link la{false, false}, lb{false, false};   // a-c and b-c: out = a->c / b->c
+                if (j == Nb.size() || (i < Na.size() && Na[i].id < Nb[j].id)) {
+                    c = Na[i].id; la = {Na[i].out, Na[i].in}; ++i;
+                } else if (i == Na.size() || Nb[j].id < Na[i].id) {
+                    c = Nb[j].id; lb = {Nb[j].out, Nb[j].in}; ++j;
+                } else {
+                    c = Na[i].id; la = {Na[i].out, Na[i].in}; lb = {Nb[j].out, Nb[j].in}; ++i; ++j;
+                }
+                if (c == a || c == b) continue;
+                const bool lac = la.out || la.in, lbc = lb.out || lb.in;
+                if (c < a) ++below; else if (c < b) ++between; else ++above;
+                // sorted vertices x<y<z and the first linked pair among (x,y), (x,z), (y,z)
+                uint32_t x, y, z;
+                if (c < a) { x = c; y = a; z = b; } else if (c < b) { x = a; y = c; z = b; } else { x = a; y = b; z = c; }
+                auto linked = [&](uint32_t p, uint32_t q) {
+                    if ((p == a && q == b) || (p == b && q == a)) return true;
+                    if (p == a || q == a) return lac;
+                    return lbc;
+                };
+                uint32_t p0, q0;
+                if (linked(x, y)) { p0 = x; q0 = y; } else if (linked(x, z)) { p0 = x; q0 = z; } else { p0 = y; q0 = z; }
+                if (!(p0 == a && q0 == b)) continue;   // counted at its first linked pair
+                // arcs among a, b, c
+                auto arc = [&](uint32_t p, uint32_t q) {
+                    if (p == a && q == b) return ab;
+                    if (p == b && q == a) return ba;
+                    if (p == a && q == c) return la.out;
+                    if (p == c && q == a) return la.in;
+                    if (p == b && q == c) return lb.out;
+                    return lb.in;   // c -> b
+                };
+                census[state_of(arc(x, y), arc(y, x), arc(y, z), arc(z, y), arc(x, z), arc(z, x))] += 1;
+            }
+            // third vertices linked to neither a nor b: the pair's link alone
+            const uint64_t n_below = a, n_between = b - a - 1, n_above = (uint64_t)n - b - 1;
+            census[state_of(false, false, ab, ba, false, false)] += n_below - below;        // roles (c, a, b)
+            census[state_of(false, false, false, false, ab, ba)] += n_between - between;    // roles (a, c, b)
+            census[state_of(ab, ba, false, false, false, false)] += n_above - above;        // roles (a, b, c)
+        }
+    }
+    u128 rest = 0;
+    for (int t = 1; t < 64; ++t) rest += census[t];
+    census[0] = choose3(n) - rest;
+    store64(census.data(), out);
+    return 0;
+}
+
 
 // Tricode -> class tables.  Return 0 on success, -1 if a code is left unclassified.
 int or_table_rules(uint8_t T[64]) {
