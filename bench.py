@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-learned", action="store_true", help="skip the learned-schedule comparison")
     p.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) run")
     p.add_argument("--no-interval", action="store_true", help="skip the interval (windowed stream) census run")
+    p.add_argument("--no-census64", action="store_true", help="skip the 64-state census run")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="measured seconds per serving arm")
     p.add_argument("--serve-warmup", type=float, default=5.0, help="unmeasured seconds before them")
     p.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
@@ -457,6 +458,44 @@ def interval_comparison(tc, torch, s, d, n, sh):
             "note": "per census: window graph build (sort, dedupe, relabel, CSR, tables) + census + D2H of 16 counts"}
 
 
+def census64_comparison(tc, torch, sh, steps=3):
+    """The 64-state census (Sec. 3, Fig. 2) on the R-MAT scale-16 graph (ef16, 20% recip, seed
+    16): one thread per linked pair merges the two lists.  Timed with CUDA events around the
+    synchronous call (id inversion, census, 512 B D2H); checked by folding the 64 states into
+    the 16 classes and comparing with the census of the same graph."""
+    import graphgen
+    n, s, d = graphgen.rmat(16, 16, 0.2, 16)
+    with tc.Graph.from_arcs(n, s, d, stream=sh, options={"algo": tc.TC_ALGO_SUFFIX}) as g:
+        info = g.stats()
+        c16 = g.census(stream=sh)
+        c64 = g.census64(stream=sh)
+        times = []
+        st = torch.cuda.ExternalStream(sh)
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            c64 = g.census64(stream=sh)
+            e1.record(st)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    table = tc.tc_tricode_table()
+    fold = [0] * 16
+    for state, k in enumerate(c64):
+        fold[int(table[state])] += k
+    ms = statistics.median(times)
+    # per linked pair both lists are read and each merged entry's original id looked up: 8 B
+    # per entry of the two lists (sum over pairs of d_r + d_s = sum_d2); 4 B per CSR entry
+    # scanned, and the offsets and id map
+    bytes_alg = 8 * info["sum_d2"] + 8 * info["e_sym"] + 16 * (n + 1)
+    peak, peak_kind = measured_peak()
+    achieved = bytes_alg / (ms * 1e-3) / 1e9
+    return {"workload": "rmat16_ef16_r20_seed16", "n": n, "arcs": len(s), "ms": ms,
+            "arcs_per_s": len(s) / (ms * 1e-3), "fold_equals_census16": fold == c16,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_census64", "bytes_alg_per_launch": bytes_alg}}
+
+
 def run_gpu(args):
     import torch
     import paper_1209_6308_gb300 as tc
@@ -548,6 +587,10 @@ def run_gpu(args):
     if not args.no_interval:
         log("interval census")
         interval_line = interval_comparison(tc, torch, s, d, n, sh)
+    census64_line = None
+    if not args.no_census64:
+        log("64-state census")
+        census64_line = census64_comparison(tc, torch, sh)
     serve_line = None
     if not args.no_serve:
         log("serving")
@@ -585,6 +628,8 @@ def run_gpu(args):
         line["learned"] = learned_line
     if interval_line is not None:
         line["interval"] = interval_line
+    if census64_line is not None:
+        line["census64"] = census64_line
     if serve_line is not None:
         line["serving"] = serve_line
     if not args.no_batch:

@@ -147,6 +147,16 @@ uint32_t tc_census_grid(const tc_options* opt);
 /* Null count C(n,3) - sum(counts[1..15]) in 128-bit (Fig. 5 steps 3-5), on the host. */
 tc_u128 tc_null_count(uint32_t n, const uint64_t counts16[16]);
 
+/* The 64-state census (Sec. 3, Fig. 2): out[s] = the number of triads in labelled state s, the
+ * arc pattern among the three actors before isomorphic states are merged into the 16 classes.
+ * The paper does not fix which actor takes which role; here they take the roles (u, v, w) in
+ * increasing vertex id of the caller's labels, and s has the tricode's bits: 1 v->u, 2 u->v,
+ * 4 v->w, 8 w->v, 16 u->w, 32 w->u (so out[0] is the null triads, C(n,3) less the rest).
+ * Merging the states through tc_tricode_table gives tc_census's 16 counts.  out: 64 host
+ * tc_u128 values.  Synchronises the stream.  Errors: TC_ERR_ARG (null argument), TC_ERR_BUSY
+ * (the graph is in use by another call), TC_ERR_OOM, TC_ERR_CUDA. */
+tc_status tc_census64(tc_graph* g, void* stream, tc_u128 out[64]);
+
 /* Census of k graphs in one persistent launch (builds a tc_batch, runs it once, frees it).
  * out16xk receives 16 uint64 per graph in the callers' order (index 0 set to the low 64 bits
  * of the null count); out003_k (may be NULL) receives each full 128-bit null count.  Host

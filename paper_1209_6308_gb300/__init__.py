@@ -106,6 +106,7 @@ SIGNATURES = {
     "tc_census_grid": (ctypes.c_uint32, [_VP]),
     "tc_census_csr_noalloc": (ctypes.c_int, [_U32, _VP, _VP, _VP, _VP]),
     "tc_null_count": (tc_u128, [_U32, ctypes.POINTER(_U64)]),
+    "tc_census64": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(tc_u128)]),
     "tc_census_batch": (ctypes.c_int, [_VP, _U32, _VP, ctypes.POINTER(_U64), ctypes.POINTER(tc_u128)]),
     "tc_batch_create": (ctypes.c_int, [_VP, _U32, _VP, _VP, ctypes.POINTER(_VP)]),
     "tc_batch_census_async": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -244,6 +245,14 @@ def tc_graph_create_csr(n: int, off, adj_flagged, stream=None, options=None) -> 
     _check(load().tc_graph_create_csr(n, po_, pa, int(dev_o), _stream_handle(stream), po, ctypes.byref(out)),
            "tc_graph_create_csr")
     return out.value
+
+
+def tc_census64(g: int, stream=None) -> list:
+    """64-state census (Sec. 3, Fig. 2): triads per labelled state, the actors in increasing
+    vertex id taking the roles u, v, w (synchronises the stream)."""
+    out = (tc_u128 * 64)()
+    _check(load().tc_census64(g, _stream_handle(stream), out), "tc_census64")
+    return [out[i].value() for i in range(64)]
 
 
 def tc_census(g: int, stream=None, options=None) -> list:
@@ -681,6 +690,9 @@ class Graph:
 
     def census(self, stream=None, options=None):
         return tc_census(self.handle, stream, options)
+
+    def census64(self, stream=None):
+        return tc_census64(self.handle, stream)
 
     def stats(self):
         return tc_graph_stats(self.handle)

@@ -196,19 +196,6 @@ tc_status upload(const T* h, uint64_t count, DevBuf& b, cudaStream_t st) {
     return TC_OK;
 }
 
-tc_u128 to_u128(unsigned __int128 x) {
-    tc_u128 r;
-    r.lo = (uint64_t)x;
-    r.hi = (uint64_t)(x >> 64);
-    return r;
-}
-
-unsigned __int128 choose3(uint64_t n) {
-    if (n < 3) return 0;
-    unsigned __int128 a = n, b = n - 1, c = n - 2;
-    return a * b * c / 6;
-}
-
 }  // namespace
 }  // namespace tc
 

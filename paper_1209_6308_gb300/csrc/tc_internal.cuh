@@ -97,4 +97,18 @@ inline unsigned grid_for(uint64_t n, unsigned block, unsigned cap = 1u << 20) {
 
 int sm_count();
 
+inline tc_u128 to_u128(unsigned __int128 x) {
+    tc_u128 r;
+    r.lo = (uint64_t)x;
+    r.hi = (uint64_t)(x >> 64);
+    return r;
+}
+
+// C(n, 3), the number of triads (Fig. 5 step 5's total), in 128 bits
+inline unsigned __int128 choose3(uint64_t n) {
+    if (n < 3) return 0;
+    unsigned __int128 a = n, b = n - 1, c = n - 2;
+    return a * b * c / 6;
+}
+
 }  // namespace tc
