@@ -33,7 +33,7 @@ tc_status cuda_fail(cudaError_t e, const char* what) {
 namespace {
 
 // The library's own stream-ordered memory pool on each device.  Freed blocks stay in it, up to
-// a quarter of the device's memory, for the next graph or call: the driver's default pool gives
+// a quarter of the device's memory, for the next graph or call: CUDA's default pool gives
 // them back at every synchronisation, so each build paid again for mapping its temporaries.
 // Persistent buffers come from the same pool on a stream of their own that is synchronised
 // at once, so they are valid on every stream when alloc_persistent returns.
