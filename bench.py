@@ -1,18 +1,23 @@
 """Benchmark of the GB300 triad census (one JSON line on rank 0).
 
-A step is one full census (Fig. 5) of the scale-20 R-MAT workload: n = 2^20, edge factor
-16, a/b/c/d = .57/.19/.19/.05, ids permuted, loops and duplicates dropped, 20% of arcs
-reciprocated, seed 2.  `value` is arcs/s with the CSR resident in HBM (device time per
-census from CUDA events on the launching stream, L2 flushed by a 512 MB write between
-steps, outside the events).  `e2e` is the same metric through the public C ABI from pinned
-host arc buffers: graph build (H2D copy, symmetrise, dedupe, relabel, sort) plus census plus
-the D2H read of the 16 counts, every step.
+A step is one full census (Fig. 5) of the R-MAT scale-26 workload, the largest single-GPU
+configuration: n = 2^26, edge factor 16, a/b/c/d = .57/.19/.19/.05, ids permuted, loops and
+duplicates dropped, 20% of arcs reciprocated, seed 3.  `value` is arcs/s with the CSR resident in
+HBM (device time per census from CUDA events on the launching stream; the inputs are far larger
+than L2 and a 512 MB write also flushes it between steps, outside the events) with the plain
+schedule; the learned schedule is timed beside it (`learned`).  `e2e` is the same metric through
+the public C ABI from pinned host arc buffers: graph build (H2D copy, symmetrise, dedupe,
+relabel, sort) plus census plus the D2H read of the 16 counts, every step.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--algo suffix|union] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--scale 26|20|10] [--impl reference]
 
---impl reference times the CPU oracle (test infrastructure, single-threaded) on a bounded
-sample of the same workload.  Under torchrun (N > 1) every rank runs the same census on its
-own GPU (replicas, weak scaling); only the barrier and the max-over-ranks time cross ranks.
+Under torchrun (N > 1) the census is sharded (paper Sec. 6-7: the connected pairs are
+independent): every rank builds the same graph, runs its contiguous share of the work
+(tc_census_shard) and the ranks sum their 16 counters with one NCCL all-reduce inside the timed
+step; `value` is the graph's arcs over the slowest rank's step time (strong scaling).
+
+--impl reference times the CPU oracle (test infrastructure; its OpenMP form on the host's cores)
+on bounded samples of the same workload.
 """
 from __future__ import annotations
 
@@ -30,37 +35,42 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "triad-census arcs/sec (bit-exact), learned/batched vs plain; % HBM roofline"
-# R-MAT workloads by scale (edge factor 16, a/b/c = .57/.19/.19, ids permuted): scale 20 is the
-# bench's default; scale 10 the small parity case; scale 26 the learned-vs-plain comparison
+# R-MAT workloads by scale (edge factor 16, a/b/c = .57/.19/.19, ids permuted): scale 26 (the
+# largest single-GPU configuration, plain vs learned) is the bench's default; scale 20 the medium
+# configuration, reported as a section; scale 10 the small parity case
 WORKLOADS = {10: dict(name="rmat10_ef16_r15_seed1", scale=10, edge_factor=16, recip=0.15, seed=1),
              20: dict(name="rmat20_ef16_r20_seed2", scale=20, edge_factor=16, recip=0.2, seed=2),
              26: dict(name="rmat26_ef16_r20_seed3", scale=26, edge_factor=16, recip=0.2, seed=3)}
-WORKLOAD = dict(WORKLOADS[20])
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_census_rmat20_traffic.txt")
+WORKLOAD = dict(WORKLOADS[26])
 CENSUS_SRC = os.path.join(ROOT, "paper_1209_6308_gb300", "csrc", "census.cu")
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--algo", default="suffix", choices=["suffix", "union"])
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--learned-reps", type=int, default=3, help="censuses per arm of the learned-vs-plain timing")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample-stride", type=int, default=0)
+    p.add_argument("--cpu-sample-seconds", type=float, default=12.0, help="target wall seconds of the CPU sample")
     p.add_argument("--no-batch", action="store_true", help="skip the 4096-graph batched comparison")
-    p.add_argument("--autotune-trials", type=int, default=12)
+    p.add_argument("--autotune-trials", type=int, default=0, help="0 = the autotuner's whole search")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-schedule comparison")
+    p.add_argument("--no-medium", action="store_true", help="skip the scale-20 section")
     p.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) run")
     p.add_argument("--no-interval", action="store_true", help="skip the interval (windowed stream) census run")
     p.add_argument("--no-census64", action="store_true", help="skip the 64-state census run")
-    p.add_argument("--serve-seconds", type=float, default=20.0, help="measured seconds per serving arm")
+    p.add_argument("--serve-seconds", type=float, default=60.0, help="measured seconds per serving arm")
     p.add_argument("--serve-warmup", type=float, default=5.0, help="unmeasured seconds before them")
     p.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
-    p.add_argument("--scale", type=int, default=20, choices=sorted(WORKLOADS), help="R-MAT workload scale")
-    a = p.parse_args()
+    p.add_argument("--serve-sweep", default="4000,8000,16000",
+                   help="further arrival rates for a short plain-schedule sweep ('' = none)")
+    p.add_argument("--sweep-seconds", type=float, default=8.0, help="measured seconds per sweep rate")
+    p.add_argument("--scale", type=int, default=26, choices=sorted(WORKLOADS), help="R-MAT workload scale")
+    a = p.parse_args(argv)
     WORKLOAD.clear()
     WORKLOAD.update(WORKLOADS[a.scale])
     return a
@@ -80,7 +90,7 @@ def log(msg: str) -> None:
 
 
 def max_over_ranks(dist, ms: float, device) -> float:
-    """The slowest rank's time: the job's time when every rank works on its own replica."""
+    """The slowest rank's time: the job's time when every rank works on its own share."""
     if dist is None:
         return ms
     import torch
@@ -89,9 +99,17 @@ def max_over_ranks(dist, ms: float, device) -> float:
     return float(t.item())
 
 
-def job_value(world: int, arcs_per_rank: int, ms: float) -> float:
-    """Whole-job arcs/s: every rank censuses its own replica, the job ends with the slowest."""
-    return world * arcs_per_rank / (ms * 1e-3)
+def job_value(arcs: int, ms: float) -> float:
+    """Whole-job arcs/s of a sharded census: the graph's arcs over the slowest rank's time (every
+    rank holds a share of one census, so the arcs are counted once)."""
+    return arcs / (ms * 1e-3)
+
+
+def bytes_alg_8d(n: int, info: dict) -> int:
+    """Algorithmic bytes of one census by the scope contract's count: the CSR read once
+    (8(n+1) offsets, 4 B per entry of the 2 e_sym list entries), each v list streamed per
+    upper pair (4 d_v) plus 16 B of offsets and pair record, and the 16 counters."""
+    return 8 * (n + 1) + 8 * info["e_sym"] + 4 * info["sum_dv_upper"] + 16 * info["e_sym"] + 128
 
 
 def dist_env():
@@ -153,26 +171,51 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle
-CPU_STRIDE = 256          # cpu_baseline: ~0.2% of the union-walk work, ~30 s on one core
-REF_STRIDE = 4096         # reference arm: per-step sample, a few seconds each
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), for the record of the CPU baseline."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
-def oracle_sample(og, stride, offset):
-    """Fig. 5 loop of the CPU oracle over vertices u = offset (mod stride); returns
-    (estimated seconds for the full census, sample seconds, work fraction)."""
-    sec, _, ws, wt = og.sample(stride, offset)
-    frac = ws / wt if wt else 1.0
-    return (sec / frac if frac > 0 else float("inf")), sec, frac
+def calibrate_stride(og, n: int, target_s: float, threads: int = 0) -> int:
+    """A vertex stride whose OpenMP sample of the Fig. 5 loop lasts about target_s: start with a
+    few dozen vertices and widen 8x at a time until a sample lasts target_s / 8, then scale."""
+    stride = 1 << max(0, n.bit_length() - 6)
+    while True:
+        sec = og.sample_parallel(stride, 0, threads)[0]
+        if sec >= target_s / 8 or stride == 1:
+            break
+        stride = max(1, stride // 8)
+    return max(1, int(stride * min(1.0, max(sec, 1e-3) / target_s)))
 
 
-def cpu_baseline(n, s, d, arcs, stride):
+def cpu_baseline(n, s, d, arcs, target_s):
+    """The oracle's OpenMP form of Fig. 5 on every host core, on a vertex sample of the same
+    graph (u = 0 mod stride, sized to about target_s of wall time), scaled to the full census by
+    the sample's share of the merge work."""
     import oracle
+    t0 = time.perf_counter()
     og = oracle.SampledGraph(n, s, d)
-    full, sec, frac = oracle_sample(og, stride, 0)
+    build_s = time.perf_counter() - t0
+    stride = calibrate_stride(og, n, target_s)
+    sec, _, ws, wt, used = og.sample_parallel(stride, 0)
     og.close()
-    return {"value": arcs / full, "unit": "arcs/s", "cores": 1, "kind": "oracle",
-            "sample": (f"single-threaded Fig. 5 oracle over vertices u = 0 (mod {stride}) of the same graph: "
-                       f"{sec:.1f} s for {frac * 100:.3f}% of the union-walk work, scaled to the full census")}
+    frac = ws / wt if wt else 1.0
+    full = sec / frac if frac > 0 else float("inf")
+    return {"value": arcs / full, "unit": "arcs/s", "cores": used, "kind": "oracle",
+            "cpu": cpu_model(), "nproc": os.cpu_count(),
+            "sample": (f"the oracle's OpenMP form of Fig. 5 (dynamic schedule, private census vectors) on {used} "
+                       f"threads over the vertices u = 0 (mod {stride}) of the same graph: {sec:.1f} s wall for "
+                       f"{frac * 100:.4f}% of the union-walk work, scaled to the full census "
+                       f"(oracle graph build {build_s:.0f} s, untimed)"),
+            "full_census_estimate_s": full}
 
 
 def run_reference(args):
@@ -182,26 +225,26 @@ def run_reference(args):
         return 0
     n, s, d = workload()
     arcs = len(s)
-    stride = args.cpu_sample_stride or REF_STRIDE
     og = oracle.SampledGraph(n, s, d)
-    times, secs, fracs = [], [], []
+    # stride for a few seconds of wall time per step, chosen before the steps
+    stride = calibrate_stride(og, n, 3.0)
+    secs, fracs, used = [], [], 1
     for i in range(args.warmup + args.steps):
-        full, sec, frac = oracle_sample(og, stride, i % stride)
+        sec, _, ws, wt, used = og.sample_parallel(stride, i % stride)
         if i >= args.warmup:
-            times.append(full)
             secs.append(sec)
-            fracs.append(frac)
+            fracs.append(ws / wt if wt else 1.0)
     og.close()
     t = sum(secs) / sum(fracs)         # pooled estimate of the full-census time
     v = arcs / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "arcs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "n": n, "arcs": arcs},
-            "cpu_baseline": {"value": v, "unit": "arcs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"step i: Fig. 5 loop over u = i (mod {stride}); full-census time "
-                                       f"estimated as total sample seconds / total work fraction "
-                                       f"({sum(fracs) * 100:.3f}% of the union-walk work)"},
+            "cpu_baseline": {"value": v, "unit": "arcs/s", "cores": used, "kind": "oracle", "cpu": cpu_model(),
+                             "sample": f"step i: the oracle's OpenMP form of Fig. 5 on {used} threads over u = i "
+                                       f"(mod {stride}); full-census time estimated as total sample seconds / "
+                                       f"total work fraction ({sum(fracs) * 100:.4f}% of the union-walk work)"},
             "e2e": {"value": v, "unit": "arcs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -225,10 +268,15 @@ def census_code_hash(text: str) -> str:
     return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
-def stored_traffic():
-    """Per-launch DRAM bytes from the committed ncu summary, if taken on this census.cu code."""
+def traffic_file(workload_name: str) -> str:
+    return os.path.join(ROOT, "profiles", f"k_census_{workload_name.split('_')[0]}_traffic.txt")
+
+
+def stored_traffic(workload_name: str = "rmat20_ef16_r20_seed2"):
+    """Per-launch DRAM bytes of k_census on a workload from the committed ncu summary, if it was
+    taken on this census.cu code (else None)."""
     try:
-        kv = dict(line.split(":", 1) for line in open(TRAFFIC_FILE) if ":" in line)
+        kv = dict(line.split(":", 1) for line in open(traffic_file(workload_name)) if ":" in line)
         if kv.get("census_code_sha256_16", "").strip() == census_code_hash(open(CENSUS_SRC).read()):
             return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -268,6 +316,7 @@ def batched_comparison(tc, torch, sh, st, trials):
         for i, h in enumerate(handles):
             tc.tc_census_async(h, loop_out[16 * i:16 * i + 16], stream=sh)
 
+    bytes_alg = sum(bytes_alg_8d(n, g.stats()) for g, (n, _, _) in zip(gs, specs))
     loop_ms = timed(loop, 2)
     b = tc.tc_batch_create(handles, stream=sh, options=opts)
     try:
@@ -290,21 +339,24 @@ def batched_comparison(tc, torch, sh, st, trials):
                                      "tuning_s": tune_s, "trials": trials},
             "speedup_vs_loop": loop_ms / min(batch_ms, tuned_ms),
             "items": n_items, "warp_blocks": n_blocks,
+            "roofline": roofline_hbm(bytes_alg, min(batch_ms, tuned_ms), "k_census (batched)"),
             "counts_identical": same_default and same_tuned}
 
 
-def learned_comparison(tc, g, stream, model, info):
+def learned_comparison(tc, g, stream, model, info, reps, bytes_alg):
     """Cost model trained on R-MAT scales 18-22 (seeds 18-22) from cycles the plain census
     measures, attached to the bench graph: census time with the plain and the learned schedule
-    (identical counts required) and the held-out cost-prediction error of both."""
+    (identical counts required), each arm's roofline, and the held-out cost-prediction error."""
     from paper_1209_6308_gb300 import learned
     learned.attach(model, g, stream=stream.cuda_stream)
-    reps = 5 if g.n <= (1 << 22) else 3
     plain_ms, plain_c = learned.census_ms(g, learned.PLAIN, stream, reps=reps)
     learned_ms, learned_c = learned.census_ms(g, learned.LEARNED, stream, reps=reps)
     q = learned.prediction_quality(model, g, stream=stream.cuda_stream)
-    return {"training": info, "plain_ms": plain_ms, "learned_ms": learned_ms,
+    return {"_plain_counts": plain_c, "training": info, "plain_ms": plain_ms, "learned_ms": learned_ms, "reps": reps,
             "speedup": plain_ms / learned_ms, "counts_identical": plain_c == learned_c,
+            "plain_arcs_per_s": None, "learned_arcs_per_s": None,
+            "roofline_plain": roofline_hbm(bytes_alg, plain_ms, "k_census (plain plan)"),
+            "roofline_learned": roofline_hbm(bytes_alg, learned_ms, "k_census (learned plan)"),
             "heldout_rms_log_cycle_error": {"model": q["rms_log_err_model"], "degree": q["rms_log_err_degree"],
                                             "vertices": q["vertices"]}}
 
@@ -424,6 +476,22 @@ def serving_comparison(tc, torch, sh, model, args):
                                           args.serve_warmup, 5)
             exact &= all(r.census() == want[rid_graph[r.id][1]] for r in res)
             out[name] = m
+        # the plain schedule at higher arrival rates, briefly: where does the p99 pass 10 ms?
+        sweep = []
+        rates = [float(x) for x in args.serve_sweep.split(",") if x.strip()]
+        for rate in rates:
+            log(f"serving sweep at {rate:.0f} req/s")
+            m, res, rid_graph = serve_arm(tc, gs, arcs, learned.PLAIN, rate, args.sweep_seconds, 2.0, 6)
+            exact &= all(r.census() == want[rid_graph[r.id][1]] for r in res)
+            sweep.append({"rate_per_s": rate, "measured_s": args.sweep_seconds, "warmup_s": 2.0,
+                          **{k: m.get(k) for k in ("requests", "p50_ms", "p99_ms", "max_ms", "arcs_per_s",
+                                                   "offered_arcs_per_s", "achieved_rate", "gpu_busy_frac",
+                                                   "overloaded")}})
+        if sweep:
+            out["sweep_plain"] = sweep
+            pts = [(out["rate_per_s"], out["plain"].get("p99_ms"))] + [(x["rate_per_s"], x["p99_ms"]) for x in sweep]
+            over = [r for r, p99 in pts if p99 is None or p99 > 10.0]
+            out["p99_above_10ms_first_rate"] = min(over) if over else None
         out["counts_identical_to_standalone"] = exact
     finally:
         for g in gs:
@@ -431,7 +499,7 @@ def serving_comparison(tc, torch, sh, model, args):
     return out
 
 
-def interval_comparison(tc, torch, s, d, n, sh):
+def interval_comparison(tc, torch, s, d, n, sh, name):
     """Interval census (the paper's monitoring use): the bench graph's arcs in a random order at
     uniform times over [0, 1000), a window of 200, a census every 100 from 200 to 1000; each
     census builds the window's graph on the device and counts it (about a fifth of the arcs)."""
@@ -452,19 +520,19 @@ def interval_comparison(tc, torch, s, d, n, sh):
             times.append((time.perf_counter() - t1) * 1e3)
             windows.append(m)
     ms = statistics.median(times)
-    return {"workload": WORKLOAD["name"] + "_times_uniform1000_window200_every100", "censuses": len(times),
+    return {"workload": name + "_times_uniform1000_window200_every100", "censuses": len(times),
             "arcs_per_window_median": int(statistics.median(windows)), "ms_per_census_median": ms,
             "arcs_per_s": statistics.median(windows) / (ms * 1e-3), "push_s": push_s,
             "note": "per census: window graph build (sort, dedupe, relabel, CSR, tables) + census + D2H of 16 counts"}
 
 
-def census64_comparison(tc, torch, sh, steps=3):
-    """The 64-state census (Sec. 3, Fig. 2) on the R-MAT scale-16 graph (ef16, 20% recip, seed
-    16): one thread per linked pair merges the two lists.  Timed with CUDA events around the
-    synchronous call (id inversion, census, 512 B D2H); checked by folding the 64 states into
-    the 16 classes and comparing with the census of the same graph."""
+def census64_comparison(tc, torch, sh, scale, steps=3):
+    """The 64-state census (Sec. 3, Fig. 2) of an R-MAT graph (ef16, 20% recip, seed = scale).
+    Timed with CUDA events around the synchronous call (id inversion, census, 1 KB D2H);
+    checked by folding the 64 states into the 16 classes and comparing with the census of the
+    same graph."""
     import graphgen
-    n, s, d = graphgen.rmat(16, 16, 0.2, 16)
+    n, s, d = graphgen.rmat(scale, 16, 0.2, scale)
     with tc.Graph.from_arcs(n, s, d, stream=sh, options={"algo": tc.TC_ALGO_SUFFIX}) as g:
         info = g.stats()
         c16 = g.census(stream=sh)
@@ -483,22 +551,42 @@ def census64_comparison(tc, torch, sh, steps=3):
     for state, k in enumerate(c64):
         fold[int(table[state])] += k
     ms = statistics.median(times)
-    # per linked pair both lists are read and each merged entry's original id looked up: 8 B
-    # per entry of the two lists (sum over pairs of d_r + d_s = sum_d2); 4 B per CSR entry
-    # scanned, and the offsets and id map
-    bytes_alg = 8 * info["sum_d2"] + 8 * info["e_sym"] + 16 * (n + 1)
+    return {"workload": f"rmat{scale}_ef16_r20_seed{scale}", "n": n, "arcs": len(s), "ms": ms,
+            "arcs_per_s": len(s) / (ms * 1e-3), "fold_equals_census16": fold == c16,
+            "roofline": roofline_hbm(bytes_alg_8d(n, info), ms, "k_census64")}
+
+
+def roofline_hbm(bytes_alg: int, ms: float, kernel: str, traffic=None, bound="hbm") -> dict:
     peak, peak_kind = measured_peak()
     achieved = bytes_alg / (ms * 1e-3) / 1e9
-    return {"workload": "rmat16_ef16_r20_seed16", "n": n, "arcs": len(s), "ms": ms,
-            "arcs_per_s": len(s) / (ms * 1e-3), "fold_equals_census16": fold == c16,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "k_census64", "bytes_alg_per_launch": bytes_alg}}
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel, "bytes_alg_per_launch": bytes_alg}
+
+
+def medium_section(tc, torch, stream, opts, steps=5):
+    """The scale-20 workload (configuration 2): census time (plain schedule), its roofline and
+    the union-walk form's time for comparison."""
+    import graphgen
+    sh = stream.cuda_stream
+    n, s, d = graphgen.rmat(20, 16, 0.2, 2)
+    from paper_1209_6308_gb300 import learned
+    with tc.Graph.from_arcs(n, s, d, stream=sh, options=opts) as g:
+        info = g.stats()
+        ms, c = learned.census_ms(g, opts, stream, reps=steps)
+        ms_union, c_union = learned.census_ms(g, {"algo": tc.TC_ALGO_UNION}, stream, reps=3)
+    c[0] = tc.tc_null_count(n, c)
+    c_union[0] = tc.tc_null_count(n, c_union)
+    return {"workload": WORKLOADS[20]["name"], "n": n, "arcs": len(s), "e_sym": info["e_sym"], "ms": ms,
+            "arcs_per_s": len(s) / (ms * 1e-3), "union_walk_ms": ms_union, "census": c,
+            "union_equals_suffix": c == c_union,
+            "roofline": dict(roofline_hbm(bytes_alg_8d(n, info), ms, "k_census", stored_traffic(), "issue"),
+                             bytes_alg_walked=info["bytes_alg"])}
 
 
 def run_gpu(args):
     import torch
     import paper_1209_6308_gb300 as tc
+    from paper_1209_6308_gb300 import shard
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -509,25 +597,35 @@ def run_gpu(args):
     algo = tc.TC_ALGO_SUFFIX if args.algo == "suffix" else tc.TC_ALGO_UNION
     opts = {"algo": algo}
     log("generating the workload")
+    t0 = time.perf_counter()
     n, s, d = workload()
+    gen_s = time.perf_counter() - t0
     arcs = len(s)
-    log(f"workload: n={n} arcs={arcs}")
+    log(f"workload: n={n} arcs={arcs} ({gen_s:.1f}s)")
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
 
+    t0 = time.perf_counter()
     g = tc.Graph.from_arcs(n, s, d, stream=sh, options=opts)
+    build_s = time.perf_counter() - t0
     info = g.stats()
-    opts_run = opts
+    log(f"graph built in {build_s:.1f}s: e_sym={info['e_sym']} sum_walk={info['sum_walk']}")
     out = torch.zeros(16, dtype=torch.int64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
-    def one_census():
-        tc.tc_census_async(g.handle, out, stream=sh, options=opts_run)
+    def one_step():
+        # this rank's shard of the census (the whole census at world 1), then the sum of the
+        # ranks' 16 counters: the one collective of the path
+        if world == 1:
+            tc.tc_census_async(g.handle, out, stream=sh, options=opts)
+        else:
+            shard.enqueue_shard(g, out, rank, world, stream=sh, options=opts)
+            shard.allreduce_counts(dist, out)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.zero_()
-            one_census()
+            one_step()
     torch.cuda.synchronize()
     log("warm-up done; timing")
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -541,56 +639,81 @@ def run_gpu(args):
             for i in range(args.steps):
                 flush.zero_()
                 starts[i].record(stream)
-                one_census()
+                one_step()
                 ends[i].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     ms = max_over_ranks(dist, statistics.mean(step_ms), "cuda")
-    counts = [int(x) & ((1 << 64) - 1) for x in out.cpu().tolist()]
-    counts[0] = tc.tc_null_count(n, counts)
+    counts = shard.census_of_sum(n, out.cpu())
+    log(f"timed: {ms:.2f} ms per step")
 
     # end to end through the C ABI from pinned host buffers
+    e2e_ms, e2e_counts = [], None
     if args.e2e_steps > 0:
         src_pin = torch.from_numpy(s.view("int32")).pin_memory()
         dst_pin = torch.from_numpy(d.view("int32")).pin_memory()
-    learned_line = None
-    model = None
-    if not args.no_learned and rank == 0:
+        log("end-to-end steps")
+        for i in range(args.e2e_steps + 1):
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = tc.tc_graph_create_arcs(n, src_pin, dst_pin, stream=sh, options=opts)
+            if world == 1:
+                c = tc.tc_census(h, stream=sh, options=opts)
+            else:
+                with torch.cuda.stream(stream):
+                    c = shard.sharded_census(h, n, out, rank, world, dist, stream=stream, options=opts)
+            dt = (time.perf_counter() - t0) * 1e3
+            tc.tc_graph_destroy(h)
+            if i:
+                e2e_ms.append(dt)
+            e2e_counts = c
+        del src_pin, dst_pin
+    e2e_job_ms = max_over_ranks(dist, statistics.mean(e2e_ms), "cuda") if e2e_ms else None
+
+    if rank != 0:
+        g.close()
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    b8d = bytes_alg_8d(n, info)
+    learned_line, model = None, None
+    if not args.no_learned:
         from paper_1209_6308_gb300 import learned
         log("training the cost model")
         model, minfo = learned.train_cost_model(scales=(18, 19, 20, 21, 22), steps=800, stream=sh)
         log(f"cost model trained: {minfo}")
-        learned_line = learned_comparison(tc, g, stream, model, minfo)
+        learned_line = learned_comparison(tc, g, stream, model, minfo, args.learned_reps, b8d)
+        learned_line["plain_arcs_per_s"] = arcs / (learned_line["plain_ms"] * 1e-3)
+        learned_line["learned_arcs_per_s"] = arcs / (learned_line["learned_ms"] * 1e-3)
+        learned_line["counts_identical_to_timed"] = learned_line.pop("_plain_counts")[1:] == counts[1:]
         log("learned comparison done")
-    e2e_ms = []
-    e2e_counts = None
-    log("end-to-end steps")
-    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        h = tc.tc_graph_create_arcs(n, src_pin, dst_pin, stream=sh, options=opts)
-        c = tc.tc_census(h, stream=sh, options=opts_run)
-        tc.tc_graph_destroy(h)
-        dt = (time.perf_counter() - t0) * 1e3
-        if i:
-            e2e_ms.append(dt)
-        e2e_counts = c
     g.close()
-    e2e_job_ms = max_over_ranks(dist, statistics.mean(e2e_ms), "cuda") if e2e_ms else None
+    del flush
+    torch.cuda.empty_cache()
 
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return 0
+    medium_line = None
+    if not args.no_medium and WORKLOAD["scale"] != 20:
+        log("scale-20 section")
+        medium_line = medium_section(tc, torch, stream, opts)
     interval_line = None
     if not args.no_interval:
         log("interval census")
-        interval_line = interval_comparison(tc, torch, s, d, n, sh)
-    census64_line = None
+        import graphgen
+        wl = WORKLOAD if WORKLOAD["scale"] <= 20 else WORKLOADS[20]
+        ni, si, di = (n, s, d) if WORKLOAD["scale"] <= 20 else graphgen.rmat(20, 16, 0.2, 2)
+        interval_line = interval_comparison(tc, torch, si, di, ni, sh, wl["name"])
+    census64_lines = None
     if not args.no_census64:
-        log("64-state census")
-        census64_line = census64_comparison(tc, torch, sh)
+        census64_lines = []
+        for sc in (16, 20):
+            log(f"64-state census, scale {sc}")
+            census64_lines.append(census64_comparison(tc, torch, sh, sc))
     serve_line = None
     if not args.no_serve:
         log("serving")
@@ -599,22 +722,22 @@ def run_gpu(args):
     if model is not None:
         tc.tc_costmodel_destroy(model)
 
-    peak, peak_kind = measured_peak()
-    bytes_alg = info["bytes_alg"]
-    achieved = bytes_alg / (ms * 1e-3) / 1e9
-    traffic = stored_traffic()
+    traffic = stored_traffic(WORKLOAD["name"])
     line = {
-        "metric": METRIC, "value": job_value(world, arcs, ms),
+        "metric": METRIC, "value": job_value(arcs, ms),
         "unit": "arcs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "n": n, "arcs": arcs, "e_sym": info["e_sym"],
-                   "algo": args.algo, "schedule": "plain", "l2": "flushed between steps (512 MB write)",
-                   "parallelism": f"replicas{world}" if world > 1 else "single"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "k_census", "bytes_alg_per_launch": bytes_alg},
-        "e2e": ({"value": job_value(world, arcs, e2e_job_ms), "unit": "arcs/s",
+                   "algo": args.algo, "schedule": "plain",
+                   "l2": "inputs far larger than L2 (CSR and tables); also flushed between steps (512 MB write)",
+                   "parallelism": f"shard{world}" if world > 1 else "single"},
+        "roofline": dict(roofline_hbm(b8d, ms / 1.0, "k_census", traffic, "issue"),
+                         bytes_alg_walked=info["bytes_alg"],
+                         note="bytes_alg_per_launch = 8(n+1) + 8 E + sum over upper pairs (4 d_v + 16) + 128; "
+                              "bytes_alg_walked = the N[v] entries the census actually walks (tc_graph_info); "
+                              "the kernel is instruction-issue bound (ncu), not HBM bound"),
+        "e2e": ({"value": job_value(arcs, e2e_job_ms), "unit": "arcs/s",
                  "h2d_bytes_per_step": 8 * arcs, "d2h_bytes_per_step": 16 * 16,
                  "ms_per_step": e2e_job_ms} if e2e_ms else None),
         "gpu_launches": args.steps,
@@ -622,14 +745,16 @@ def run_gpu(args):
         "census": counts,
         "census_e2e_equal": (e2e_counts == counts) if e2e_counts else None,
         "step_ms": {"min": min(step_ms), "max": max(step_ms)},
-        "timed_wall_s": wall,
+        "timed_wall_s": wall, "generate_s": gen_s, "build_s": build_s,
     }
     if learned_line is not None:
         line["learned"] = learned_line
+    if medium_line is not None:
+        line["medium"] = medium_line
     if interval_line is not None:
         line["interval"] = interval_line
-    if census64_line is not None:
-        line["census64"] = census64_line
+    if census64_lines is not None:
+        line["census64"] = census64_lines
     if serve_line is not None:
         line["serving"] = serve_line
     if not args.no_batch:
@@ -637,7 +762,7 @@ def run_gpu(args):
         line["batched"] = batched_comparison(tc, torch, sh, stream, args.autotune_trials)
     if not args.no_cpu_baseline:
         log("cpu baseline")
-        line["cpu_baseline"] = cpu_baseline(n, s, d, arcs, args.cpu_sample_stride or CPU_STRIDE)
+        line["cpu_baseline"] = cpu_baseline(n, s, d, arcs, args.cpu_sample_seconds)
     log("done")
     print(json.dumps(line), flush=True)
     if dist:

@@ -140,6 +140,26 @@ tc_status tc_census_async(tc_graph* g, void* stream, const tc_options* opt, uint
 tc_status tc_census_profile(tc_graph* g, void* stream, const tc_options* opt, uint64_t* d_out16,
                             uint64_t* d_vcost, uint64_t* d_phase);
 
+/* One rank's share of a census sharded over `world` GPUs (paper Sec. 6-7: the connected pairs
+ * (u, v) of Fig. 5 step 2.1 are independent units of work, so any partition of them sums to the
+ * census).  The census's work - the plan's CTA work items in order, then the vertices handled
+ * one warp each, in id order - is cut into `world` contiguous shards of about equal work
+ * (the plan's exact per-pair work units), and this call runs shard `rank` (0 <= rank < world,
+ * else TC_ERR_ARG).  Every rank holds the same graph.  d_out16 (device, 16 uint64) receives
+ * this shard's counts of classes 1..15 (index 0 = 0), as tc_census_async does; summing the
+ * world shards' outputs (an all-reduce of 16 uint64) gives the census's classes 1..15, and
+ * tc_null_count of that sum gives the null count.  The first call for a plan and a world
+ * computes the shards and synchronises `stream`; later calls only enqueue.  TC_ERR_BUSY if the
+ * graph is in use by another call; TC_ERR_RANGE if world > 2^20. */
+tc_status tc_census_shard(tc_graph* g, void* stream, const tc_options* opt, uint32_t rank, uint32_t world,
+                          uint64_t* d_out16);
+
+/* Where the shards of tc_census_shard start: bounds[2r] = the first CTA work item and
+ * bounds[2r+1] = the first one-warp-per-vertex id of shard r, for r = 0..world (r = world: the
+ * item count and the end of that tier's id range).  Host array of 2 (world + 1) uint32.
+ * Synchronises `stream` when the shards are not yet computed. */
+tc_status tc_census_shard_bounds(tc_graph* g, void* stream, const tc_options* opt, uint32_t world, uint32_t* bounds);
+
 /* Number of CTAs the census launches on the current device for these options (opt may be
  * NULL): the length / 3 of d_phase above. */
 uint32_t tc_census_grid(const tc_options* opt);
@@ -209,16 +229,20 @@ const char* tc_last_error(void);
  * their own pool).  The paper has no counterpart to this entry point.
  *
  * Input: a device CSR in this library's form, as tc_graph_device_csr returns it: d_off[n+1]
- * (uint64) and d_adj (uint32 (id << 2) | dir, ascending per list, symmetric), with vertex
- * degrees not increasing with the id.  Output: d_out16 (device, 16 uint64) as for
- * tc_census_async (index 0 = 0; get the null count with tc_null_count).
+ * (uint64, starting at 0 and never decreasing) and d_adj[d_off[n]] (uint32 (id << 2) | dir,
+ * ids < n, no self-loops, dir != 0, strictly ascending per list, symmetric with mirrored dir
+ * bits), with vertex degrees not increasing with the id.  Every one of these rules is checked
+ * on the device before the census runs (the checks read only inside the lists that the offsets
+ * define), and a CSR that breaks one gives TC_ERR_ARG with nothing launched after the check.
+ * Output: d_out16 (device, 16 uint64) as for tc_census_async (index 0 = 0; get the null count
+ * with tc_null_count).
  * Scratch: one fixed 8 MiB device array inside the library, so n <= 2^20 (larger n gives
- * TC_ERR_RANGE, as does a graph needing more than 2^18 work items); lists out of degree order
- * give TC_ERR_ARG.  Every GPU that loads the library holds the array until the process exits.
- * The first call on a device looks up the array's device address; make that first call
- * before any stream capture.  All calls share the array and it keeps the last call's
- * contents, so calls that overlap on the GPU race: serialise them.  The call synchronises
- * `stream` while it sizes the work, then enqueues the census and returns. */
+ * TC_ERR_RANGE, as does a graph needing more than 2^18 work items).  Every GPU that loads the
+ * library holds the array until the process exits.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents, so calls that overlap on the GPU race:
+ * serialise them.  The call synchronises `stream` while it checks the CSR and sizes the work,
+ * then enqueues the census and returns. */
 tc_status tc_census_csr_noalloc(uint32_t n, const uint64_t* d_off, const uint32_t* d_adj, void* stream,
                                 uint64_t* d_out16);
 

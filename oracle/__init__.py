@@ -59,6 +59,9 @@ def _load():
         lib.or_graph_free.argtypes = [ctypes.c_void_p]
         lib.or_census_bm_sample.restype = ctypes.c_double
         lib.or_census_bm_sample.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, u64p, u64p, u64p]
+        lib.or_census_bm_sample_parallel.restype = ctypes.c_double
+        lib.or_census_bm_sample_parallel.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+                                                     u64p, u64p, u64p, ctypes.POINTER(ctypes.c_int)]
         _lib = lib
     return _lib
 
@@ -180,6 +183,18 @@ class SampledGraph:
         wt = np.zeros(1, dtype=np.uint64)
         sec = _load().or_census_bm_sample(self._h, stride, offset, _p64(out), _p64(ws), _p64(wt))
         return sec, _u128(out, 16), int(ws[0]), int(wt[0])
+
+    def sample_parallel(self, stride: int, offset: int = 0, threads: int = 0):
+        """The same sample with the sampled vertices shared by OpenMP threads (the paper's CPU
+        form): (wall seconds, partial counts, merge work of the sample, total merge work,
+        threads used)."""
+        out = np.zeros(32, dtype=np.uint64)
+        ws = np.zeros(1, dtype=np.uint64)
+        wt = np.zeros(1, dtype=np.uint64)
+        used = ctypes.c_int(0)
+        sec = _load().or_census_bm_sample_parallel(self._h, stride, offset, threads, _p64(out), _p64(ws), _p64(wt),
+                                                   ctypes.byref(used))
+        return sec, _u128(out, 16), int(ws[0]), int(wt[0]), int(used.value)
 
     def close(self):
         if self._h:

@@ -104,6 +104,8 @@ SIGNATURES = {
     "tc_census_async": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "tc_census_profile": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "tc_census_grid": (ctypes.c_uint32, [_VP]),
+    "tc_census_shard": (ctypes.c_int, [_VP, _VP, _VP, _U32, _U32, _VP]),
+    "tc_census_shard_bounds": (ctypes.c_int, [_VP, _VP, _VP, _U32, _VP]),
     "tc_census_csr_noalloc": (ctypes.c_int, [_U32, _VP, _VP, _VP, _VP]),
     "tc_null_count": (tc_u128, [_U32, ctypes.POINTER(_U64)]),
     "tc_census64": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(tc_u128)]),
@@ -294,6 +296,24 @@ def tc_census_csr_noalloc(n: int, d_off: int, d_adj: int, d_out16, stream=None) 
     if not dev:
         raise ValueError("d_out16 must be device memory")
     _check(load().tc_census_csr_noalloc(n, d_off, d_adj, _stream_handle(stream), p), "tc_census_csr_noalloc")
+
+
+def tc_census_shard(g: int, d_out16, rank: int, world: int, stream=None, options=None) -> None:
+    """Shard `rank` of `world` of the census of g (Sec. 6-7: independent pairs): its counts of
+    classes 1..15 into d_out16 (16 uint64 on the device); the shards' sum is the census."""
+    p, dev, keep = _buffer(d_out16, np.uint64)
+    if not dev:
+        raise ValueError("d_out16 must be device memory")
+    po, keepo = _options(options)
+    _check(load().tc_census_shard(g, _stream_handle(stream), po, rank, world, p), "tc_census_shard")
+
+
+def tc_census_shard_bounds(g: int, world: int, stream=None, options=None) -> np.ndarray:
+    """[(first item, first warp-tier vertex) for r = 0..world] as a (world + 1, 2) uint32 array."""
+    b = np.zeros(2 * (world + 1), np.uint32)
+    po, keepo = _options(options)
+    _check(load().tc_census_shard_bounds(g, _stream_handle(stream), po, world, b.ctypes.data), "tc_census_shard_bounds")
+    return b.reshape(world + 1, 2)
 
 
 def tc_census_grid(options=None) -> int:

@@ -369,6 +369,48 @@ tc_status tc_census_profile(tc_graph* g, void* stream, const tc_options* opt, ui
                           reinterpret_cast<unsigned long long*>(d_vcost), reinterpret_cast<unsigned long long*>(d_phase));
 }
 
+tc_status tc_census_shard(tc_graph* g, void* stream, const tc_options* opt, uint32_t rank, uint32_t world,
+                          uint64_t* d_out16) {
+    if (!g || !d_out16) return fail(TC_ERR_ARG, "null argument");
+    if (world == 0 || rank >= world) return fail(TC_ERR_ARG, "tc_census_shard: need 0 <= rank < world");
+    if (world > (1u << 20)) return fail(TC_ERR_RANGE, "tc_census_shard: world above 2^20");
+    cudaStream_t st = (cudaStream_t)stream;
+    Opts o;
+    TC_TRY(resolve_opts(opt, &g->s.opts, &o));
+    std::unique_lock<std::mutex> lk(g->s.busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(TC_ERR_BUSY, "graph is in use by another call");
+    census_fit_chunk(g->s, o);
+    Plan* p = nullptr;
+    TC_TRY(get_plan(g->s, o, st, &p));
+    TC_TRY(plan_shards(g->s, o, *p, world, st));
+    const uint32_t* b = p->shard_bounds.data();
+    const uint32_t i0 = b[2 * rank], i1 = b[2 * rank + 2];
+    const uint32_t v0 = b[2 * rank + 1], v1 = b[2 * rank + 3];
+    TC_CUDA(cudaMemsetAsync(d_out16, 0, sizeof(uint64_t) * 16, st));
+    return census_enqueue_range(g->s, o, p->items.as<Item>() + i0, i1 - i0, p->warp_begin + v0, p->warp_begin + v1, st,
+                                reinterpret_cast<unsigned long long*>(d_out16));
+}
+
+tc_status tc_census_shard_bounds(tc_graph* g, void* stream, const tc_options* opt, uint32_t world, uint32_t* bounds) {
+    if (!g || !bounds) return fail(TC_ERR_ARG, "null argument");
+    if (world == 0) return fail(TC_ERR_ARG, "tc_census_shard_bounds: world must be >= 1");
+    if (world > (1u << 20)) return fail(TC_ERR_RANGE, "tc_census_shard_bounds: world above 2^20");
+    cudaStream_t st = (cudaStream_t)stream;
+    Opts o;
+    TC_TRY(resolve_opts(opt, &g->s.opts, &o));
+    std::unique_lock<std::mutex> lk(g->s.busy, std::try_to_lock);
+    if (!lk.owns_lock()) return fail(TC_ERR_BUSY, "graph is in use by another call");
+    census_fit_chunk(g->s, o);
+    Plan* p = nullptr;
+    TC_TRY(get_plan(g->s, o, st, &p));
+    TC_TRY(plan_shards(g->s, o, *p, world, st));
+    for (uint32_t r = 0; r <= world; ++r) {
+        bounds[2 * r] = p->shard_bounds[2 * r];
+        bounds[2 * r + 1] = p->warp_begin + p->shard_bounds[2 * r + 1];
+    }
+    return TC_OK;
+}
+
 uint32_t tc_census_grid(const tc_options* opt) {
     Opts o;
     if (resolve_opts(opt, nullptr, &o) != TC_OK) return 0;

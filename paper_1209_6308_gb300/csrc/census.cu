@@ -29,6 +29,7 @@
 // handled one warp per vertex after the items run out, in the same persistent launch.
 #include <atomic>
 #include <cstring>
+#include <vector>
 
 #include "graph.cuh"
 #include "plan.cuh"
@@ -865,6 +866,73 @@ __global__ void k_plan_items(GraphDev g, PlanArgs a, const uint32_t* __restrict_
     }
 }
 
+// ---------------------------------------------------------------- shards (multi-GPU partition)
+// The work of the census is a sequence: the plan's CTA items in order, then the one-warp-per-
+// vertex tier's vertices in id order.  A shard is a contiguous range of that sequence of about
+// 1/world of its work (Sec. 6-7: the pairs (u, v) are independent, so any partition of them
+// sums to the census).  Work is counted in the plan's units (plan.cuh).
+
+// units[i] = the work of item i, one warp per item (clamped to 2^32 - 1)
+__global__ void k_item_units(GraphDev g, const Item* __restrict__ items, uint32_t n_items, uint32_t chunk, int algo,
+                             uint32_t* units) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < n_items; i += warps) {
+        const Item it = items[i];
+        const uint64_t ubase = g.off[it.u];
+        const uint32_t du = (uint32_t)(g.off[it.u + 1] - ubase), upu = g.up[it.u];
+        const uint32_t chunks = (du + chunk - 1) / chunk;
+        unsigned long long w = 0;
+        for (uint32_t j = it.j0 + lane; j < it.j1; j += 32) w += pair_units(g, it.u, ubase, du, upu, j, chunks, algo);
+        for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0) units[i] = w < 0xffffffffull ? (uint32_t)w : 0xffffffffu;
+    }
+}
+
+// units[x] = the work of warp-tier vertex wb + x (its at most warp_max_deg pairs)
+__global__ void k_vertex_units(GraphDev g, uint32_t wb, uint32_t we, int algo, uint32_t* units) {
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < we - wb; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = wb + (uint32_t)x;
+        const uint64_t ubase = g.off[u];
+        const uint32_t du = (uint32_t)(g.off[u + 1] - ubase), upu = g.up[u];
+        unsigned long long w = 0;
+        for (uint32_t j = upu; j < du; ++j) w += pair_units(g, u, ubase, du, upu, j, 1u, algo);
+        units[x] = w < 0xffffffffull ? (uint32_t)w : 0xffffffffu;
+    }
+}
+
+// smallest i in [0, n] with pre[i] >= t (pre ascending, n + 1 entries)
+__device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t* pre, uint32_t n, unsigned long long t) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre[mid] < t) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Shard r's start in the sequence: out[2r] = first item, out[2r+1] = first warp-tier vertex
+// (relative to the tier's start), for r = 0..world (r = world: the ends).  The cut for r sits
+// at r/world of the total work; a cut inside the items starts the shard at the first item
+// whose prefix reaches it, one inside the vertices likewise.
+__global__ void k_shard_bounds(const uint64_t* __restrict__ ipre, uint32_t ni, const uint64_t* __restrict__ vpre,
+                               uint32_t nv, uint32_t world, uint32_t* out) {
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r <= world; r += gridDim.x * blockDim.x) {
+        const unsigned long long Ti = ipre[ni], T = Ti + vpre[nv];
+        const unsigned long long t = (T / world) * r + (T % world) * r / world;
+        uint32_t i = ni, v = 0;
+        if (r == world) {
+            v = nv;
+        } else if (t <= Ti) {
+            i = lower_bound_u64(ipre, ni, t);
+        } else {
+            v = lower_bound_u64(vpre, nv, t - Ti);
+        }
+        out[2 * r] = i;
+        out[2 * r + 1] = v;
+    }
+}
+
 std::atomic<uint64_t> g_table_uploaded{0};
 constexpr int kForms = 5;   // single graph without tables; single graph with tables, with and without the
                             // map; batch and wave (tables and map)
@@ -936,6 +1004,8 @@ tc_status get_plan(GraphStore& g, const Opts& o, cudaStream_t st, Plan** out) {
     Plan& p = g.plans[g.next_plan];
     g.next_plan = (g.next_plan + 1) % GraphStore::kPlans;
     p.valid = false;
+    p.shard_world = 0;
+    p.shard_bounds.clear();
     p.items.release();
     p.key = o;
     const GraphDev gd = g.dev();
@@ -1115,8 +1185,48 @@ tc_status census_launch_raw(const GraphDev& gd, const Opts& o, const Item* items
     return TC_OK;
 }
 
+tc_status plan_shards(GraphStore& g, const Opts& o, Plan& p, uint32_t world, cudaStream_t st) {
+    if (p.shard_world == world) return TC_OK;
+    const GraphDev gd = g.dev();
+    const uint32_t ni = p.n_items, nv = p.warp_end - p.warp_begin;
+    DevBuf iu, vu, ipre, vpre, bounds;
+    TC_TRY(iu.alloc(sizeof(uint32_t) * (ni ? ni : 1), st));
+    TC_TRY(vu.alloc(sizeof(uint32_t) * (nv ? nv : 1), st));
+    TC_TRY(ipre.alloc(sizeof(uint64_t) * (ni + 1ull), st));
+    TC_TRY(vpre.alloc(sizeof(uint64_t) * (nv + 1ull), st));
+    TC_TRY(bounds.alloc(sizeof(uint32_t) * 2ull * (world + 1ull), st));
+    if (ni) {
+        k_item_units<<<grid_for((uint64_t)ni * 32, 256, 8192), 256, 0, st>>>(gd, p.items.as<Item>(), ni, o.chunk,
+                                                                             (int)o.algo, iu.as<uint32_t>());
+        TC_LAUNCH("k_item_units");
+    }
+    if (nv) {
+        k_vertex_units<<<grid_for(nv, 256, 8192), 256, 0, st>>>(gd, p.warp_begin, p.warp_end, (int)o.algo,
+                                                                vu.as<uint32_t>());
+        TC_LAUNCH("k_vertex_units");
+    }
+    TC_TRY(scan_u32_to_u64(iu.as<uint32_t>(), ipre.as<uint64_t>(), ni, st));
+    TC_TRY(scan_u32_to_u64(vu.as<uint32_t>(), vpre.as<uint64_t>(), nv, st));
+    k_shard_bounds<<<grid_for(world + 1ull, 256, 64), 256, 0, st>>>(ipre.as<uint64_t>(), ni, vpre.as<uint64_t>(), nv,
+                                                                     world, bounds.as<uint32_t>());
+    TC_LAUNCH("k_shard_bounds");
+    std::vector<uint32_t> h(2ull * (world + 1ull));
+    TC_CUDA(cudaMemcpyAsync(h.data(), bounds.p, sizeof(uint32_t) * h.size(), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    p.shard_bounds.swap(h);
+    p.shard_world = world;
+    return TC_OK;
+}
+
 tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16,
                          unsigned long long* d_vcost, unsigned long long* d_phase) {
+    return census_enqueue_range(g, o, p.items.as<Item>(), p.n_items, p.warp_begin, p.warp_end, st, d_out16, d_vcost,
+                                d_phase);
+}
+
+tc_status census_enqueue_range(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
+                               uint32_t warp_end, cudaStream_t st, unsigned long long* d_out16,
+                               unsigned long long* d_vcost, unsigned long long* d_phase) {
     if (g.e_sym == 0) return TC_OK;
     const bool vt = g.vs.p != nullptr;
     const bool map = census_map(g, o);
@@ -1125,11 +1235,11 @@ tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream
     TC_CUDA(cudaMemsetAsync(g.ctr.p, 0, sizeof(uint32_t) * 4, st));
     Params P;
     P.g = g.dev();
-    P.items = p.items.as<Item>();
-    P.n_items = p.n_items;
-    P.warp_begin = p.warp_begin;
-    P.warp_end = p.warp_end;
-    P.wshift = warp_block_shift(p.warp_end - p.warp_begin, (unsigned)census_grid(o));
+    P.items = items;
+    P.n_items = n_items;
+    P.warp_begin = warp_begin;
+    P.warp_end = warp_end;
+    P.wshift = warp_block_shift(warp_end - warp_begin, (unsigned)census_grid(o));
     P.chunk = o.chunk;
     P.warp_max = o.warp_max_deg;
     P.ctr = g.ctr.as<uint32_t>();
@@ -1139,8 +1249,6 @@ tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream
     P.graphs = nullptr;
     P.wblocks = nullptr;
     P.n_wblocks = 0;
-    P.reqs = nullptr;
-    P.n_reqs = 0;
     P.reqs = nullptr;
     P.n_reqs = 0;
     const unsigned grid = (unsigned)census_grid(o);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <mutex>
+#include <vector>
 
 #include "tc_internal.cuh"
 
@@ -47,6 +48,11 @@ struct Plan {
     DevBuf items;
     uint32_t n_items = 0;
     uint32_t warp_begin = 0, warp_end = 0;
+    // shards of the plan's work for shard_world ranks (plan_shards): rank r runs items
+    // [shard_bounds[2r], shard_bounds[2r+2]) and warp-tier vertices warp_begin +
+    // [shard_bounds[2r+1], shard_bounds[2r+3]); 0 = not computed
+    uint32_t shard_world = 0;
+    std::vector<uint32_t> shard_bounds;
 };
 
 struct GraphStore {
@@ -117,6 +123,14 @@ void census_fit_chunk(const GraphStore& g, Opts& o);
 // d_phase (optional, [3 * CTAs] uint64) the globaltimer at start, end of items, end per CTA.
 tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream_t st, unsigned long long* d_out16,
                          unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr);
+// The same census over a part of a plan: items[0, n_items) and warp-tier vertices
+// [warp_begin, warp_end) (a shard; census_enqueue runs the whole plan).
+tc_status census_enqueue_range(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
+                               uint32_t warp_end, cudaStream_t st, unsigned long long* d_out16,
+                               unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr);
+// Cut p's work into `world` contiguous shards of about equal work (cached in p for that world);
+// synchronises st when it computes them.
+tc_status plan_shards(GraphStore& g, const Opts& o, Plan& p, uint32_t world, cudaStream_t st);
 int census_grid(const Opts& o);
 // log2 of the vertices a warp takes per grab in the one-warp-per-vertex tier, for `vertices`
 // such vertices and a grid of `grid` CTAs (0..5).

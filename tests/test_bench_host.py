@@ -24,7 +24,7 @@ def _rank_main(rank, world, port, times, out):
     try:
         dist.barrier()
         ms = bench.max_over_ranks(dist, times[rank], "cpu")
-        out.put((rank, ms, bench.job_value(world, 1000, ms)))
+        out.put((rank, ms, bench.job_value(1000, ms)))
     finally:
         dist.destroy_process_group()
 
@@ -44,13 +44,13 @@ def test_max_over_ranks_and_job_value_with_two_gloo_ranks():
         assert p.exitcode == 0
     for rank, ms, value in res:
         assert ms == 40.0                      # every rank sees the slowest rank's time
-        assert value == pytest.approx(2 * 1000 / 0.040)
+        assert value == pytest.approx(1000 / 0.040)   # one census's arcs: the ranks shard it
 
 
 def test_single_process_reduction_is_the_identity():
     import bench
     assert bench.max_over_ranks(None, 3.25, "cpu") == 3.25
-    assert bench.job_value(1, 500, 2.0) == pytest.approx(250000.0)
+    assert bench.job_value(500, 2.0) == pytest.approx(250000.0)
 
 
 def test_defaults_finish_in_minutes(monkeypatch):
@@ -58,10 +58,10 @@ def test_defaults_finish_in_minutes(monkeypatch):
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = bench.parse()
     assert a.gpus == 1 and a.warmup >= 3 and 1 <= a.steps <= 20
-    assert a.impl == "ours" and a.serve_seconds <= 30
+    assert a.impl == "ours" and a.serve_seconds == 60.0 and bench.WORKLOAD["scale"] == 26
 
 
-@pytest.mark.parametrize("argv,scale", [([], 20), (["--scale", "26"], 26), (["--scale", "10"], 10), ([], 20)])
+@pytest.mark.parametrize("argv,scale", [([], 26), (["--scale", "20"], 20), (["--scale", "10"], 10), ([], 26)])
 def test_workload_follows_the_scale_option(monkeypatch, argv, scale):
     import bench
     monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
@@ -82,6 +82,13 @@ def test_reference_arm_on_other_ranks_exits_without_work(monkeypatch):
     assert not called
 
 
+def test_bytes_alg_follows_the_scope_formula():
+    """8(n+1) + 8 E + sum over upper pairs (4 d_v + 16) + 128, from the graph's statistics."""
+    import bench
+    info = {"e_sym": 10, "sum_dv_upper": 37}
+    assert bench.bytes_alg_8d(5, info) == 8 * 6 + 8 * 10 + 4 * 37 + 16 * 10 + 128
+
+
 def test_census_code_hash_ignores_comments_only():
     """The stored DRAM traffic stays valid across comment edits of census.cu, not code edits."""
     import bench
@@ -90,6 +97,6 @@ def test_census_code_hash_ignores_comments_only():
     other = "int a = 1;\nint b = 3;\n"
     assert bench.census_code_hash(src) == bench.census_code_hash(same)
     assert bench.census_code_hash(src) != bench.census_code_hash(other)
-    with open(bench.TRAFFIC_FILE) as f:
+    with open(bench.traffic_file("rmat20_ef16_r20_seed2")) as f:
         kv = dict(line.split(":", 1) for line in f if ":" in line and not line.startswith("#"))
     assert "census_code_sha256_16" in kv and float(kv["dram_bytes_per_launch"]) > 0

@@ -220,6 +220,36 @@ def test_samples_partition_the_census():
     assert work == wt and tot[1:] == oracle.census_bm(n, s, d)[1:]
 
 
+def test_parallel_samples_partition_the_census_like_the_serial_ones():
+    """The OpenMP form of the timing sample (the paper's CPU form) gives the same partial
+    counts and work as the serial sample, and its samples over u = k (mod 4) add up to the
+    connected part of the census."""
+    n, s, d = graphgen.rmat(9, 16, 0.2, 3)
+    og = oracle.SampledGraph(n, s, d)
+    tot, work = [0] * 16, 0
+    for k in range(4):
+        sec, part, ws, wt, used = og.sample_parallel(4, k, threads=3)
+        _, part1, ws1, wt1 = og.sample(4, k)
+        assert part == part1 and ws == ws1 and wt == wt1 and sec >= 0 and used >= 1
+        tot = [a + b for a, b in zip(tot, part)]
+        work += ws
+    og.close()
+    assert work == wt and tot[1:] == oracle.census_bm(n, s, d)[1:]
+
+
+def test_unsorted_and_sorted_inputs_build_the_same_graph():
+    """The oracle skips its sort for inputs already sorted by (src, dst): the census is the
+    same for a shuffled copy with duplicates and loops."""
+    n, s, d = graphgen.rmat(9, 16, 0.2, 3)
+    rng = np.random.default_rng(1)
+    s2 = np.concatenate([s, s[:50], np.arange(5, dtype=np.uint32)])
+    d2 = np.concatenate([d, d[:50], np.arange(5, dtype=np.uint32)])
+    p = rng.permutation(len(s2))
+    a = oracle.census_bm(n, s, d, with_stats=True)
+    b = oracle.census_bm(n, s2[p], d2[p], with_stats=True)
+    assert a[0] == b[0] and b[1] == (a[1][0], 5, 50)
+
+
 def test_networkx_triadic_census_agrees():
     nx = pytest.importorskip("networkx")
     for (n, s, d) in (graphgen.rmat(8, 16, 0.15, 1), graphgen.gnp(50, 0.1, 2), graphgen.chung_lu(500, 8, 2.1, 0.1, 4, 3)):
