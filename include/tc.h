@@ -55,7 +55,14 @@ typedef enum {
     /* Same census; the w that only u reaches and that lie past v are classified in bulk
      * from per-list direction-class counts instead of one by one (only dir(u,v) and
      * dir(u,w) decide their class), so each pair costs O(|N[v]|). */
-    TC_ALGO_SUFFIX = 1
+    TC_ALGO_SUFFIX = 1,
+    /* Same census; the one-sided third vertices of each pair are counted in bulk as in
+     * TC_ALGO_SUFFIX, and the common neighbours of all pairs are found once per triangle
+     * (a < b < c met once, walking the lower-id neighbours of c against those of b), whose
+     * tricode fixes the triad and its corrections to the three pairs' bulk and dyadic
+     * counts (steps 2.1.2 - 2.1.4).  Needs the per upper pair tables every built graph has;
+     * warp_max_deg <= 128.  Not offered by the batched launch or the server. */
+    TC_ALGO_TRIANGLE = 2
 } tc_algo;
 
 /* How the connected pairs (u,v) are grouped into GPU work items. */
@@ -198,10 +205,21 @@ tc_status tc_batch_census_async(tc_batch* b, void* stream, uint64_t* d_out16xk);
 /* Replay and return host counts as for tc_census_batch.  Synchronises `stream`. */
 tc_status tc_batch_census(tc_batch* b, void* stream, uint64_t* out16xk, tc_u128* out003_k);
 
-/* Autotuner: time the batch under candidate tile and tier thresholds (warp_max_deg,
- * chunk_entries, ctas_per_sm, item_work; at most max_trials of them, 0 = all), keep the
- * fastest plan in the batch and report its options and median time per launch in ms. */
+/* Autotuner: time the batch under candidate kernel forms and tile and tier thresholds by
+ * coordinate descent from the batch's current options - algo {union, suffix}, warp_max_deg
+ * {16..256}, chunk_entries {1024..8192}, ctas_per_sm {2, 3, 4}, item_work {sized to the
+ * graphs, 2^14..2^22} - one at a time, keeping the best value of each, for up to three passes
+ * or until a pass gains under 1% (at most max_trials timed plans, 0 = no limit; each timed as
+ * the median of three replays after one untimed one).  Keeps the fastest plan in the batch and
+ * reports its options and median time per launch in ms.  Synchronises `stream`. */
 tc_status tc_batch_autotune(tc_batch* b, void* stream, uint32_t max_trials, tc_options* best, float* best_ms);
+
+/* The trials of the batch's last autotune, in the order they ran (options and median ms). */
+typedef struct {
+    tc_options opts;
+    float ms;
+} tc_autotune_trial;
+tc_status tc_batch_autotune_history(const tc_batch* b, tc_autotune_trial* out, uint32_t max, uint32_t* count);
 
 /* Work counts of the batch's current plan (either pointer may be NULL). */
 tc_status tc_batch_stats(const tc_batch* b, uint32_t* n_items, uint32_t* n_warp_blocks);

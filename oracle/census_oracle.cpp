@@ -201,21 +201,39 @@ bool build_digraph(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* 
     e.erase(std::unique(e.begin(), e.end()), e.end());
     g.arcs = e.size();
     g.dups = m - g.loops - g.arcs;
+    // out[x]: the arcs are sorted by source, so x's out-neighbours are one run of e; in[x]: a
+    // counting placement by target.  Both filled (and the lists merged) vertex by vertex, the
+    // vertices shared among OpenMP threads when there are many: the lists are the same.
+    const int64_t N64 = (int64_t)n;
+    std::vector<uint64_t> ostart(n + 1ull, 0), istart(n + 1ull, 0);
+    for (auto& p : e) { ++ostart[p.first + 1ull]; ++istart[p.second + 1ull]; }
+    for (uint64_t x = 0; x < n; ++x) { ostart[x + 1] += ostart[x]; istart[x + 1] += istart[x]; }
+    std::vector<uint32_t> inflat(e.size());
+    {
+        std::vector<uint64_t> pos(istart.begin(), istart.end() - 1);
+        for (auto& p : e) inflat[pos[p.second]++] = p.first;   // e is sorted: each run ascends
+    }
     g.out.assign(n, {});
     std::vector<std::vector<uint32_t>> in(n);
-    for (auto& p : e) { g.out[p.first].push_back(p.second); in[p.second].push_back(p.first); }
     g.N.assign(n, {});
-    for (uint32_t x = 0; x < n; ++x) {
+#pragma omp parallel for schedule(dynamic, 4096) if (n > 100000)
+    for (int64_t xi = 0; xi < N64; ++xi) {
+        const uint32_t x = (uint32_t)xi;
+        g.out[x].reserve(ostart[x + 1] - ostart[x]);
+        for (uint64_t k = ostart[x]; k < ostart[x + 1]; ++k) g.out[x].push_back(e[k].second);
+        in[x].assign(inflat.begin() + istart[x], inflat.begin() + istart[x + 1]);
         std::sort(in[x].begin(), in[x].end());
         // merge out[x] and in[x] into one tagged sorted list
         size_t i = 0, j = 0;
         const auto& o = g.out[x];
         const auto& q = in[x];
+        g.N[x].reserve(o.size() + q.size());
         while (i < o.size() || j < q.size()) {
             if (j == q.size() || (i < o.size() && o[i] < q[j])) { g.N[x].push_back({o[i], true, false}); ++i; }
             else if (i == o.size() || q[j] < o[i]) { g.N[x].push_back({q[j], false, true}); ++j; }
             else { g.N[x].push_back({o[i], true, true}); ++i; ++j; }
         }
+        std::vector<uint32_t>().swap(in[x]);
     }
     return true;
 }

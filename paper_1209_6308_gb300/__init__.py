@@ -21,7 +21,7 @@ CLASS_NAMES = ("003", "012", "102", "021D", "021U", "021C", "111D", "111U",
                "030T", "030C", "201", "120D", "120U", "120C", "210", "300")
 
 TC_OK, TC_ERR_ARG, TC_ERR_RANGE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_BUSY = range(7)
-TC_ALGO_UNION, TC_ALGO_SUFFIX = 0, 1
+TC_ALGO_UNION, TC_ALGO_SUFFIX, TC_ALGO_TRIANGLE = 0, 1, 2
 TC_SCHED_PLAIN, TC_SCHED_LEARNED = 0, 1
 
 
@@ -42,6 +42,10 @@ class tc_options(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_uint32), ("schedule", ctypes.c_uint32), ("warp_max_deg", ctypes.c_uint32),
                 ("chunk_entries", ctypes.c_uint32), ("item_work", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("map_mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 9)]
+
+
+class tc_autotune_trial(ctypes.Structure):
+    _fields_ = [("opts", tc_options), ("ms", ctypes.c_float)]
 
 
 class tc_graph_info(ctypes.Structure):
@@ -115,6 +119,7 @@ SIGNATURES = {
     "tc_batch_census": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_U64), ctypes.POINTER(tc_u128)]),
     "tc_batch_autotune": (ctypes.c_int, [_VP, _VP, _U32, _VP, ctypes.POINTER(ctypes.c_float)]),
     "tc_batch_stats": (ctypes.c_int, [_VP, ctypes.POINTER(_U32), ctypes.POINTER(_U32)]),
+    "tc_batch_autotune_history": (ctypes.c_int, [_VP, _VP, _U32, ctypes.POINTER(_U32)]),
     "tc_batch_destroy": (None, [_VP]),
     "tc_costmodel_num_params": (ctypes.c_uint32, []),
     "tc_costmodel_create": (ctypes.c_int, [_U64, ctypes.POINTER(_VP)]),
@@ -382,6 +387,16 @@ def tc_batch_autotune(b: int, max_trials: int = 0, stream=None):
     best = {k: int(getattr(o, k)) for k in ("algo", "schedule", "warp_max_deg", "chunk_entries", "item_work",
                                              "ctas_per_sm")}
     return best, float(ms.value)
+
+
+def tc_batch_autotune_history(b: int, max_trials: int = 1024) -> list:
+    """The last autotune's trials in order: [(options dict, median ms)]."""
+    arr = (tc_autotune_trial * max(max_trials, 1))()
+    cnt = _U32()
+    _check(load().tc_batch_autotune_history(b, ctypes.addressof(arr), max_trials, ctypes.byref(cnt)),
+           "tc_batch_autotune_history")
+    keys = ("algo", "schedule", "warp_max_deg", "chunk_entries", "item_work", "ctas_per_sm")
+    return [({k: int(getattr(arr[i].opts, k)) for k in keys}, float(arr[i].ms)) for i in range(cnt.value)]
 
 
 def tc_batch_stats(b: int):

@@ -148,16 +148,21 @@ Opts merge_opts(const tc_options* in, const Opts* base) {
 
 tc_status resolve_opts(const tc_options* in, const Opts* base, Opts* out) {
     Opts o = merge_opts(in, base);
-    if (o.algo > TC_ALGO_SUFFIX) return fail(TC_ERR_ARG, "unknown algo");
+    if (o.algo > TC_ALGO_TRIANGLE) return fail(TC_ERR_ARG, "unknown algo");
     if (o.schedule > TC_SCHED_LEARNED) return fail(TC_ERR_ARG, "unknown schedule");
     // the suffix form's hash takes 4 slots per entry, the union walk's 2 plus the sorted copy:
     // both fill about 70 KB of shared memory, three CTAs per SM
+    // the triangle form's CTAs hold a small hash (2 slots per staged entry) and few registers:
+    // eight per SM keep the most loads in flight
     if (!o.chunk) {
-        o.chunk = o.algo == TC_ALGO_SUFFIX ? 2048u : 4096u;
+        o.chunk = o.algo == TC_ALGO_UNION ? 4096u : 2048u;
         o.chunk_auto = true;
     }
-    if (!o.ctas_per_sm) o.ctas_per_sm = 3;
-    const uint32_t max_chunk = o.algo == TC_ALGO_SUFFIX ? 8192u : 16384u;   // shared-memory hash sizes
+    if (!o.ctas_per_sm) o.ctas_per_sm = o.algo == TC_ALGO_TRIANGLE ? 8 : 3;
+    const uint32_t max_chunk = o.algo == TC_ALGO_UNION ? 16384u : 8192u;   // shared-memory hash sizes
+    // the triangle form stages a warp-tier vertex's lower neighbours in a 256-slot warp hash
+    if (o.algo == TC_ALGO_TRIANGLE && o.warp_max_deg > 128)
+        return fail(TC_ERR_ARG, "warp_max_deg must be <= 128 for the triangle form");
     if (o.chunk < 512 || o.chunk > max_chunk || (o.chunk & (o.chunk - 1)))
         return fail(TC_ERR_ARG, "chunk_entries must be a power of two in [512, 16384] (8192 for the suffix form)");
     if (o.warp_max_deg > o.chunk / 8) return fail(TC_ERR_ARG, "warp_max_deg must be <= chunk_entries / 8");
@@ -387,8 +392,11 @@ tc_status tc_census_shard(tc_graph* g, void* stream, const tc_options* opt, uint
     const uint32_t i0 = b[2 * rank], i1 = b[2 * rank + 2];
     const uint32_t v0 = b[2 * rank + 1], v1 = b[2 * rank + 3];
     TC_CUDA(cudaMemsetAsync(d_out16, 0, sizeof(uint64_t) * 16, st));
+    // the triangle form's bulk pair sums: an even slice of the vertices
+    const uint32_t na = g->s.n_active;
+    const uint32_t b0 = (uint32_t)((uint64_t)na * rank / world), b1 = (uint32_t)((uint64_t)na * (rank + 1) / world);
     return census_enqueue_range(g->s, o, p->items.as<Item>() + i0, i1 - i0, p->warp_begin + v0, p->warp_begin + v1, st,
-                                reinterpret_cast<unsigned long long*>(d_out16));
+                                reinterpret_cast<unsigned long long*>(d_out16), nullptr, nullptr, b0, b1);
 }
 
 tc_status tc_census_shard_bounds(tc_graph* g, void* stream, const tc_options* opt, uint32_t world, uint32_t* bounds) {

@@ -110,6 +110,7 @@ struct BatchStore {
     cudaGraphExec_t exec = nullptr;
     unsigned long long* h_out = nullptr;
     std::vector<uint64_t> woff_h;
+    std::vector<tc_autotune_trial> history;   // the last autotune's trials, in order
 
     ~BatchStore() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -241,6 +242,8 @@ tc_status tc_batch_create(tc_graph* const* gs, uint32_t k, const tc_options* opt
     BatchStore& B = b->s;
     B.k = k;
     tc_status s = resolve_opts(opt, nullptr, &B.opts);
+    if (s == TC_OK && B.opts.algo == TC_ALGO_TRIANGLE)
+        s = fail(TC_ERR_ARG, "the batched launch runs the union or suffix form");
     for (uint32_t i = 0; s == TC_OK && i < k; ++i)
         if (!gs[i]) s = fail(TC_ERR_ARG, "null graph in batch");
     if (s == TC_OK) {
@@ -309,63 +312,119 @@ tc_status tc_batch_census(tc_batch* b, void* stream, uint64_t* out16xk, tc_u128*
     return TC_OK;
 }
 
+namespace {
+
+tc_options to_options(const Opts& o) {
+    tc_options t;
+    std::memset(&t, 0, sizeof(t));
+    t.algo = o.algo;
+    t.schedule = o.schedule;
+    t.warp_max_deg = o.warp_max_deg;
+    t.chunk_entries = o.chunk;
+    t.item_work = o.item_work;
+    t.ctas_per_sm = o.ctas_per_sm;
+    return t;
+}
+
+bool valid_batch_opts(const Opts& o) {
+    const uint32_t max_chunk = o.algo == TC_ALGO_UNION ? 16384u : 8192u;
+    return o.chunk >= 512 && o.chunk <= max_chunk && o.warp_max_deg <= o.chunk / 8 && o.ctas_per_sm >= 1 &&
+           o.ctas_per_sm <= 8;
+}
+
+}  // namespace
+
 tc_status tc_batch_autotune(tc_batch* b, void* stream, uint32_t max_trials, tc_options* best_out, float* best_ms) {
     if (!b) return fail(TC_ERR_ARG, "null batch");
     BatchStore& B = b->s;
     cudaStream_t st = (cudaStream_t)stream;
+    B.history.clear();
     if (B.k == 0) return TC_OK;
     const Opts base = B.opts;
-    // the current plan first, then the grid of tile and tier thresholds
-    std::vector<Opts> cand{base};
-    for (uint32_t wm : {16u, 32u, 64u})
-        for (uint32_t ch : {2048u, 4096u})
-            for (uint32_t cps : {3u, 4u})
-                for (uint32_t iw : {1u << 16, 1u << 18}) {
-                    Opts o = base;
-                    o.warp_max_deg = wm;
-                    o.chunk = ch;
-                    o.ctas_per_sm = cps;
-                    o.item_work = iw;
-                    if (!(o == base)) cand.push_back(o);
-                }
-    if (max_trials && max_trials < cand.size()) cand.resize(max_trials);
     cudaEvent_t e0, e1;
     TC_CUDA(cudaEventCreate(&e0));
     TC_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    Opts best_o = base;
     tc_status s = TC_OK;
-    for (const Opts& o : cand) {
+    // median of three timed replays after one untimed one; +inf when the plan cannot be made
+    auto measure = [&](const Opts& o, float* ms) -> tc_status {
+        *ms = 1e30f;
+        if (!valid_batch_opts(o)) return TC_OK;
         B.opts = o;
-        s = batch_plan(B, st);
-        if (s != TC_OK) break;
+        tc_status r = batch_plan(B, st);
+        if (r == TC_ERR_ARG) return TC_OK;   // e.g. shared memory beyond this GPU's limit
+        if (r != TC_OK) return r;
         float ts[3];
-        for (int r = 0; r < 4 && s == TC_OK; ++r) {
-            if (cudaEventRecord(e0, st) != cudaSuccess) s = fail(TC_ERR_CUDA, "event");
-            if (s == TC_OK) s = batch_run(B, st);
-            if (s == TC_OK && cudaEventRecord(e1, st) != cudaSuccess) s = fail(TC_ERR_CUDA, "event");
-            if (s == TC_OK && cudaEventSynchronize(e1) != cudaSuccess) s = fail(TC_ERR_CUDA, "event sync");
-            if (s == TC_OK && r > 0) cudaEventElapsedTime(&ts[r - 1], e0, e1);
+        for (int k = 0; k < 4; ++k) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) return fail(TC_ERR_CUDA, "event");
+            TC_TRY(batch_run(B, st));
+            if (cudaEventRecord(e1, st) != cudaSuccess) return fail(TC_ERR_CUDA, "event");
+            if (cudaEventSynchronize(e1) != cudaSuccess) return fail(TC_ERR_CUDA, "event sync");
+            if (k > 0) cudaEventElapsedTime(&ts[k - 1], e0, e1);
         }
-        if (s != TC_OK) break;
         std::sort(ts, ts + 3);
-        if (ts[1] < best) { best = ts[1]; best_o = o; }
+        *ms = ts[1];
+        B.history.push_back({to_options(o), ts[1]});
+        return TC_OK;
+    };
+    // coordinate descent from the current options: each pass varies one threshold at a time
+    // over its range, keeping the best value found, until a pass improves nothing by 1% or the
+    // trial budget (0 = none) is spent
+    Opts best_o = base;
+    float best = 1e30f;
+    s = measure(base, &best);
+    uint32_t trials = 1;
+    for (int pass = 0; s == TC_OK && pass < 3; ++pass) {
+        const float pass_start = best;
+        for (int dim = 0; dim < 5 && s == TC_OK; ++dim) {
+            std::vector<uint32_t> vals;
+            if (dim == 0) vals = {TC_ALGO_UNION, TC_ALGO_SUFFIX};
+            if (dim == 1) vals = {16u, 32u, 64u, 128u, 256u};
+            if (dim == 2) vals = {1024u, 2048u, 4096u, 8192u};
+            if (dim == 3) vals = {2u, 3u, 4u};
+            if (dim == 4) vals = {0u, 1u << 14, 1u << 16, 1u << 18, 1u << 20, 1u << 22};
+            for (uint32_t v : vals) {
+                if (max_trials && trials >= max_trials) break;
+                Opts o = best_o;
+                if (dim == 0) o.algo = v;
+                if (dim == 1) o.warp_max_deg = v;
+                if (dim == 2) o.chunk = v;
+                if (dim == 3) o.ctas_per_sm = v;
+                if (dim == 4) o.item_work = v;
+                if (o == best_o) continue;
+                bool seen = false;
+                for (const auto& h : B.history) {
+                    const tc_options t = to_options(o);
+                    seen |= std::memcmp(&h.opts, &t, sizeof(t)) == 0;
+                }
+                if (seen) continue;
+                float ms;
+                s = measure(o, &ms);
+                ++trials;
+                if (s != TC_OK) break;
+                if (ms < best) {
+                    best = ms;
+                    best_o = o;
+                }
+            }
+        }
+        if (best > 0.99f * pass_start) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     B.opts = best_o;
     TC_TRY(batch_plan(B, st));
     if (s != TC_OK) return s;
-    if (best_out) {
-        std::memset(best_out, 0, sizeof(*best_out));
-        best_out->algo = best_o.algo;
-        best_out->schedule = best_o.schedule;
-        best_out->warp_max_deg = best_o.warp_max_deg;
-        best_out->chunk_entries = best_o.chunk;
-        best_out->item_work = best_o.item_work;
-        best_out->ctas_per_sm = best_o.ctas_per_sm;
-    }
+    if (best_out) *best_out = to_options(best_o);
     if (best_ms) *best_ms = best;
+    return TC_OK;
+}
+
+tc_status tc_batch_autotune_history(const tc_batch* b, tc_autotune_trial* out, uint32_t max, uint32_t* count) {
+    if (!b || !count || (max && !out)) return fail(TC_ERR_ARG, "null argument");
+    const auto& h = b->s.history;
+    const uint32_t c = (uint32_t)std::min<size_t>(h.size(), max);
+    for (uint32_t i = 0; i < c; ++i) out[i] = h[i];
+    *count = c;
     return TC_OK;
 }
 

@@ -64,6 +64,7 @@ struct GraphStore {
     DevBuf ctr;        // census work counters (uint32 x 4)
     DevBuf acc;        // census accumulators (uint64 x 16)
     DevBuf cost;       // optional per-vertex predicted cost (float x n) for the learned schedule
+    DevBuf tri;        // triangle form: bulk sums and triangle tricode histogram (uint64 x 96)
     Opts opts;
     static constexpr int kPlans = 4;
     Plan plans[kPlans];
@@ -125,9 +126,23 @@ tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream
                          unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr);
 // The same census over a part of a plan: items[0, n_items) and warp-tier vertices
 // [warp_begin, warp_end) (a shard; census_enqueue runs the whole plan).
+// The triangle form's bulk pair sums run for the vertices [bulk_v0, bulk_v1) (whole graph by
+// default; a shard takes its own slice).
 tc_status census_enqueue_range(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
                                uint32_t warp_end, cudaStream_t st, unsigned long long* d_out16,
-                               unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr);
+                               unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr,
+                               uint32_t bulk_v0 = 0, uint32_t bulk_v1 = 0xffffffffu);
+// TC_ALGO_TRIANGLE (triangles.cu): bulk pair sums for [bulk_v0, bulk_v1), the triangle tricode
+// histogram over the given items and warp-tier range, and the fold into d_out16[1..15].
+tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items,
+                                  uint32_t warp_begin, uint32_t warp_end, uint32_t bulk_v0, uint32_t bulk_v1,
+                                  cudaStream_t st, unsigned long long* d_out16, unsigned long long* d_vcost);
+// The triangle walk alone: histogram of the 64 tricodes (old == nullptr) or of the 64 states in
+// the caller's id order (old = original id per vertex, d_perm_state = [9][64] state of a
+// tricode per rank pattern) of every triangle, added into d_hist64; ctr: 4 zeroed uint32.
+tc_status triangles_launch(const GraphDev& gd, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
+                           uint32_t warp_end, uint32_t* ctr, const uint32_t* old, const uint8_t* d_perm_state,
+                           unsigned long long* d_hist64, unsigned long long* d_vcost, cudaStream_t st);
 // Cut p's work into `world` contiguous shards of about equal work (cached in p for that world);
 // synchronises st when it computes them.
 tc_status plan_shards(GraphStore& g, const Opts& o, Plan& p, uint32_t world, cudaStream_t st);

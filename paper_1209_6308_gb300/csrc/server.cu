@@ -637,6 +637,7 @@ tc_status tc_server_create(const tc_server_options* opt, tc_server** out) {
     if (o.lanes > (uint32_t)kMaxLanes) return fail(TC_ERR_ARG, "lanes must be <= 4");
     std::unique_ptr<tc_server> s(new tc_server());
     TC_TRY(resolve_opts(&o.census, nullptr, &s->opts));
+    if (s->opts.algo == TC_ALGO_TRIANGLE) return fail(TC_ERR_ARG, "the server runs the union or suffix form");
     if (s->opts.schedule != TC_SCHED_PLAIN && s->opts.schedule != TC_SCHED_LEARNED)
         return fail(TC_ERR_ARG, "unknown schedule");
     s->max_active = o.max_active ? o.max_active : 1024;

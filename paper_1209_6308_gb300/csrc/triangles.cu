@@ -1,0 +1,440 @@
+// triangles.cu - the census with the common neighbours enumerated once per triangle.
+//
+// For a connected pair (u, v), u < v (Fig. 5 step 2.1), every third vertex w of
+// S = N[u] u N[v] \ {u, v} that only one endpoint reaches has a class fixed by two direction
+// bits (dir(u,v) and the link of w to that endpoint), so those triads are counted in bulk
+// from the per upper pair tables' direction-class suffix counts; only the common neighbours
+// need their full tricode (the union-free rewrite of step 2.1.4).  The suffix kernel finds
+// each pair's common neighbours by walking N[v] past u.  Here each common neighbour is found
+// once, as a triangle: with ids in descending degree, L(x) = the neighbours of x with smaller
+// ids (a prefix of N[x]) is short for every x, and the triangle a < b < c is met exactly
+// once, when the walk of L(c) for the pair (b, c) finds a in L(b), staged in shared memory.
+// Its tricode (roles (a, b, c)) then gives every correction it makes to the pairs' bulk
+// counts (Fig. 5 steps 2.1.2 - 2.1.4):
+//   + the triad itself, counted once at the pair (a, b) with w = c > b (step 2.1.4's rule);
+//   - c among the u-only third vertices of (a, b) and among its v-only ones, b among the
+//     v-only ones of (a, c): common neighbours, not one-sided;
+//   + one common neighbour in the dyadic count n - |S| - 2 of each of its three pairs.
+// So the kernel only histograms the 64 tricodes of the triangles; a small fold kernel turns
+// them and the bulk sums into the 16 classes on the device.
+//
+// The same walk in the caller's id order (the triangle's state with its actors ordered by
+// their original ids) serves the 64-state census (census64.cu).
+//
+// Work: a vertex b with degree above the warp tier becomes CTA items (b, range of its upper
+// pairs (b, c)), cut by the plan (plan.cuh) with pair work |L(c)|; the CTA stages L(b) in a
+// shared-memory hash, and its warps walk the lists L(c) of 32 pairs at a time as one
+// flattened range, so short and long lists share the lanes.  The other vertices run one warp
+// each, with L(b) in the warp's own hash.
+#include <atomic>
+#include <cstring>
+
+#include "graph.cuh"
+
+namespace tc {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr uint32_t kWarpSlots = 256;     // per-warp hash slots: |L(b)| <= warp_max_deg <= 128
+constexpr uint32_t kFlushElems = 1u << 30;
+
+__device__ __forceinline__ uint32_t tri_hash(uint32_t x, int hb) { return (x * 2654435761u) >> (32 - hb); }
+
+// tricode of the triangle (a, b, c) from three stored entries: e_ba = a in N[b] (bits seen from
+// b: 1 b->a, 2 a->b), e_bc = c in N[b] (1 b->c, 2 c->b), e_ca = a in N[c] (1 c->a, 2 a->c).
+// Tricode bits: 1 b->a, 2 a->b, 4 b->c, 8 c->b, 16 a->c, 32 c->a.
+__device__ __forceinline__ uint32_t tri_code(uint32_t e_ba, uint32_t e_bc, uint32_t e_ca) {
+    return (e_ba & 3u) | ((e_bc & 3u) << 2) | (((e_ca >> 1) & 1u) << 4) | ((e_ca & 1u) << 5);
+}
+
+struct TriParams {
+    GraphDev g;
+    const Item* items;
+    uint32_t n_items;
+    uint32_t warp_begin, warp_end;
+    uint32_t wshift;              // warp tier: 2^wshift consecutive vertices per grab
+    uint32_t chunk;               // entries of L(b) staged per pass of a CTA item (hash: 2 x chunk slots)
+    uint32_t* ctr;                // [0] next item, [1] next warp-tier vertex
+    const uint32_t* old;          // OLD: the caller's id of each vertex
+    const uint8_t* perm_state;    // OLD: [9][64] state of a tricode under the rank pattern 3 ra + rb
+    unsigned long long* hist;     // 64 bins (triangle tricodes, or states with OLD)
+    unsigned long long* vcost;    // optional [n]: SM cycles per CTA-tier vertex b
+};
+
+// Walk the lists L(c) of the pairs (b, c = N[b][j]), j in [j0, j1), 32 pairs per batch, and
+// count each a of L(c) found in the staged hash of L(b).  One warp; the lanes share each
+// batch's flattened (pair, position) range.  Returns the entries walked (warp-uniform).
+template <bool OLD>
+__device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, uint64_t bbase, uint32_t j0, uint32_t j1,
+                                               const uint32_t* sH, const uint32_t* sO, int hb, uint32_t hmask,
+                                               uint32_t ob, const uint8_t* sPerm, uint32_t* myHist, int lane) {
+    const uint64_t* __restrict__ off = P.g.off;
+    const uint32_t* __restrict__ adj = P.g.adj;
+    const uint32_t* __restrict__ up = P.g.up;
+    const uint32_t le_mask = (2u << lane) - 1u;
+    uint32_t walked = 0;
+    for (uint32_t jb = j0; jb < j1; jb += 32) {
+        const uint32_t j = jb + lane;
+        const bool ok = j < j1;
+        uint32_t e_bc = ok ? adj[bbase + j] : 0u;
+        const uint32_t c = e_bc >> 2;
+        uint64_t cb = ok ? off[c] : 0ull;
+        uint32_t len = ok ? up[c] : 0u;
+        uint32_t oc = (OLD && ok) ? P.old[c] : 0u;
+        // compact the pairs with a non-empty L(c) into lanes 0 .. cnt-1
+        const uint32_t nz = __ballot_sync(0xffffffffu, len != 0u);
+        if (!nz) continue;
+        const uint32_t cnt = __popc(nz);
+        const uint32_t src = __fns(nz, 0, lane + 1) & 31u;
+        e_bc = __shfl_sync(0xffffffffu, e_bc, src);
+        cb = __shfl_sync(0xffffffffu, cb, src);
+        len = __shfl_sync(0xffffffffu, len, src);
+        if (OLD) oc = __shfl_sync(0xffffffffu, oc, src);
+        if ((uint32_t)lane >= cnt) len = 0u;
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t excl = incl - len;
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        walked += total;
+        int seg_prev = -1;
+        // two rounds of 32 entries per iteration, so each lane has two loads in flight
+        for (uint32_t base = 0; base < total; base += 64) {
+            // the pairs whose range starts in a round mark their start; lane i's pair is the
+            // last one started at or before the round's entry i
+            const bool stA = (uint32_t)lane < cnt && excl >= base && excl < base + 32u;
+            const bool stB = (uint32_t)lane < cnt && excl >= base + 32u && excl < base + 64u;
+            const uint32_t MA = __reduce_or_sync(0xffffffffu, stA ? (1u << (excl - base)) : 0u);
+            const uint32_t MB = __reduce_or_sync(0xffffffffu, stB ? (1u << (excl - base - 32u)) : 0u);
+            const int segA = seg_prev + __popc(MA & le_mask);
+            const int lastA = __shfl_sync(0xffffffffu, segA, 31);
+            const int segB = lastA + __popc(MB & le_mask);
+            seg_prev = __shfl_sync(0xffffffffu, segB, 31);
+            const uint32_t sa = (uint32_t)segA & 31u, sb = (uint32_t)segB & 31u;
+            const uint32_t PA = __shfl_sync(0xffffffffu, excl, sa), PB = __shfl_sync(0xffffffffu, excl, sb);
+            const uint64_t BA = __shfl_sync(0xffffffffu, cb, sa), BB = __shfl_sync(0xffffffffu, cb, sb);
+            const uint32_t EA = __shfl_sync(0xffffffffu, e_bc, sa), EB = __shfl_sync(0xffffffffu, e_bc, sb);
+            uint32_t OA = 0, OB = 0;
+            if (OLD) {
+                OA = __shfl_sync(0xffffffffu, oc, sa);
+                OB = __shfl_sync(0xffffffffu, oc, sb);
+            }
+            const uint32_t iA = base + lane, iB = base + 32u + lane;
+            const uint32_t xA = iA < total ? __ldg(adj + BA + (iA - PA)) : 0u;
+            const uint32_t xB = iB < total ? __ldg(adj + BB + (iB - PB)) : 0u;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const uint32_t e_ca = r ? xB : xA;
+                if (!e_ca) continue;
+                const uint32_t a = e_ca >> 2;
+                uint32_t h = tri_hash(a, hb);
+                uint32_t e = sH[h];
+                while (e != 0u && (e >> 2) != a) {
+                    h = (h + 1u) & hmask;
+                    e = sH[h];
+                }
+                if (e != 0u) {
+                    uint32_t t = tri_code(e, r ? EB : EA, e_ca);
+                    if (OLD) {
+                        const uint32_t oa = sO[h], oc2 = r ? OB : OA;
+                        const uint32_t ra = (oa > ob) + (oa > oc2), rb = (ob > oa) + (ob > oc2);
+                        t = sPerm[(3u * ra + rb) * 64u + t];
+                    }
+                    atomicAdd(&myHist[t], 1u);
+                }
+            }
+        }
+    }
+    return walked;
+}
+
+// Add a warp's 64 bins to the graph's histogram and clear them (one warp).
+__device__ __forceinline__ void flush_warp_hist(uint32_t* myHist, unsigned long long* hist, int lane) {
+    __syncwarp();
+    for (int t = lane; t < 64; t += 32) {
+        const uint32_t v = myHist[t];
+        if (v) atomicAdd(&hist[t], (unsigned long long)v);
+        myHist[t] = 0u;
+    }
+    __syncwarp();
+}
+
+template <bool OLD>
+__global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t slots = 2u * P.chunk;
+    uint32_t* sH = reinterpret_cast<uint32_t*>(smem);                 // [slots] CTA hash of L(b)
+    uint32_t* sO = sH + slots;                                         // [slots] OLD: caller ids
+    uint32_t* sWH = sO + (OLD ? slots : 0u);                           // [kWarps][kWarpSlots]
+    uint32_t* sWO = sWH + kWarps * kWarpSlots;                         // [kWarps][kWarpSlots] OLD
+    uint32_t* sHist = sWO + (OLD ? kWarps * kWarpSlots : 0u);         // [kWarps][64]
+    uint8_t* sPerm = reinterpret_cast<uint8_t*>(sHist + kWarps * 64);  // [9][64] OLD
+    __shared__ uint32_t s_item, s_next;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int k = tid; k < kWarps * 64; k += kThreads) sHist[k] = 0u;
+    if (OLD)
+        for (int k = tid; k < 9 * 64; k += kThreads) sPerm[k] = P.perm_state[k];
+    __syncthreads();
+    uint32_t* myHist = sHist + warp * 64;
+    const uint64_t* __restrict__ off = P.g.off;
+    const uint32_t* __restrict__ adj = P.g.adj;
+    const uint32_t* __restrict__ up = P.g.up;
+    uint32_t since_flush = 0;   // warp-uniform: entries walked since this warp's bins were flushed
+
+    // ---------------------------------------------------------------- CTA items
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&P.ctr[0], 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= P.n_items) break;
+        const Item w = P.items[it];
+        const long long t0 = clock64();
+        const uint32_t b = w.u;
+        const uint64_t bbase = off[b];
+        const uint32_t lb = up[b];
+        const uint32_t ob = OLD ? P.old[b] : 0u;
+        // L(b) = N[b][0, lb), staged `chunk` entries per pass; every pass walks the item's pairs
+        for (uint32_t c0 = 0; c0 < lb; c0 += P.chunk) {
+            const uint32_t LA = min(P.chunk, lb - c0);
+            int hb = 6;
+            while ((1u << hb) < 2u * LA) ++hb;
+            const uint32_t H = 1u << hb, hmask = H - 1u;
+            for (uint32_t k = tid; k < H; k += kThreads) sH[k] = 0u;
+            if (tid == 0) s_next = w.j0;
+            __syncthreads();
+            for (uint32_t k = tid; k < LA; k += kThreads) {
+                const uint32_t e = adj[bbase + c0 + k];
+                uint32_t h = tri_hash(e >> 2, hb);
+                while (atomicCAS(&sH[h], 0u, e) != 0u) h = (h + 1u) & hmask;
+                if (OLD) sO[h] = P.old[e >> 2];
+            }
+            __syncthreads();
+            for (;;) {
+                uint32_t jb = 0;
+                if (lane == 0) jb = atomicAdd(&s_next, 32u);
+                jb = __shfl_sync(0xffffffffu, jb, 0);
+                if (jb >= w.j1) break;
+                since_flush += walk_pairs<OLD>(P, bbase, jb, min(jb + 32u, w.j1), sH, sO, hb, hmask, ob, sPerm, myHist,
+                                               lane);
+                if (since_flush >= kFlushElems) {
+                    flush_warp_hist(myHist, P.hist, lane);
+                    since_flush = 0;
+                }
+            }
+            __syncthreads();   // every warp is done with this pass before the hash is replaced
+        }
+        if (P.vcost && tid == 0) atomicAdd(&P.vcost[b], (unsigned long long)(clock64() - t0));
+        __syncthreads();   // every thread has read s_item before thread 0 takes the next item
+    }
+
+    // ---------------------------------------------------------------- one warp per vertex
+    uint32_t* wH = sWH + warp * kWarpSlots;
+    uint32_t* wO = sWO + (OLD ? warp * kWarpSlots : 0u);
+    for (;;) {
+        uint32_t vb = 0;
+        if (lane == 0) vb = atomicAdd(&P.ctr[1], 1u << P.wshift);
+        vb = __shfl_sync(0xffffffffu, vb, 0);
+        if (vb >= P.warp_end - P.warp_begin) break;
+        const uint32_t b0 = P.warp_begin + vb, b1 = min(b0 + (1u << P.wshift), P.warp_end);
+        for (uint32_t b = b0; b < b1; ++b) {
+            const uint64_t bbase = off[b];
+            const uint32_t db = (uint32_t)(off[b + 1] - bbase), lb = up[b];
+            if (lb == 0u || lb >= db) continue;   // no lower or no upper neighbour: no triangle has b in the middle
+            int hb = 6;
+            while ((1u << hb) < 2u * lb) ++hb;
+            const uint32_t hmask = (1u << hb) - 1u;
+            __syncwarp();
+            for (uint32_t k = lane; k < (1u << hb); k += 32) wH[k] = 0u;
+            __syncwarp();
+            for (uint32_t k = lane; k < lb; k += 32) {
+                const uint32_t e = adj[bbase + k];
+                uint32_t h = tri_hash(e >> 2, hb);
+                while (atomicCAS(&wH[h], 0u, e) != 0u) h = (h + 1u) & hmask;
+                if (OLD) wO[h] = P.old[e >> 2];
+            }
+            __syncwarp();
+            since_flush += walk_pairs<OLD>(P, bbase, lb, db, wH, wO, hb, hmask, OLD ? P.old[b] : 0u, sPerm, myHist,
+                                           lane);
+            if (since_flush >= kFlushElems) {
+                flush_warp_hist(myHist, P.hist, lane);
+                since_flush = 0;
+            }
+        }
+    }
+    flush_warp_hist(myHist, P.hist, lane);
+}
+
+// Bulk counts of the pairs (u, v) with u in [v0, v1), one warp per u, the lanes over its upper
+// pairs: per dir(u,v) code c (tricode bits 1|2, 1..3), raw[7(c-1) + d - 1] += the entries of
+// N[v] past u with direction class d (v-only third vertices before the common ones come
+// off), raw[7(c-1) + 3 + d - 1] += those of N[u] past v (u-only), raw[7(c-1) + 6] += the
+// dyadic base n - d_u - d_v (steps 2.1.2 - 2.1.3 before the common neighbours).
+__global__ void k_pair_bulk(GraphDev g, uint32_t v0, uint32_t v1, unsigned long long* raw) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long acc[3][7];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 7; ++k) acc[c][k] = 0ull;
+    const unsigned long long n = g.n;
+    for (uint64_t x = v0 + ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5); x < v1; x += warps) {
+        const uint32_t u = (uint32_t)x;
+        const uint64_t ubase = g.off[u];
+        const uint32_t du = (uint32_t)(g.off[u + 1] - ubase), upu = g.up[u];
+        const uint64_t pb = g.ub[u] - upu;
+        for (uint32_t j = upu + lane; j < du; j += 32) {
+            const uint32_t e = g.adj[ubase + j], v = e >> 2, duv = e & 3u;
+            const uint32_t cuv = ((duv & 1u) << 1) | (duv >> 1);
+            const uint32_t dv = (uint32_t)(g.off[v + 1] - g.off[v]);
+            const uint2 vs = g.vs[pb + j], us = g.us[pb + j];
+            const uint32_t vlen = dv - 1u - g.rp[pb + j], ulen = du - 1u - j;
+            const unsigned long long val[7] = {vs.x, vs.y, (unsigned long long)(vlen - vs.x - vs.y),
+                                               us.x, us.y, (unsigned long long)(ulen - us.x - us.y),
+                                               n - du - dv};
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (cuv == (uint32_t)(c + 1))
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) acc[c][k] += val[k];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            unsigned long long s = acc[c][k];
+            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0 && s) atomicAdd(&raw[7 * c + k], s);
+        }
+}
+
+struct Table64 {
+    uint8_t t[64];
+};
+
+// 16 classes from the bulk sums and the triangle tricodes (see the file comment); adds
+// classes 1..15 into out16 (index 0 untouched).  One block of 64 threads.
+__global__ void k_tri_fold(const unsigned long long* __restrict__ raw, const unsigned long long* __restrict__ hist,
+                           Table64 T, unsigned long long* out16) {
+    __shared__ unsigned long long s[16];
+    const uint32_t t = threadIdx.x;
+    if (t < 16) s[t] = 0ull;
+    __syncthreads();
+    if (t < 21) {
+        const uint32_t c = t / 7 + 1, k = t % 7;
+        const unsigned long long v = raw[t];
+        uint32_t cls;
+        if (k < 3) cls = T.t[c | ((k + 1) << 2)];          // v-only: dir(v,w) = k + 1
+        else if (k < 6) cls = T.t[c | ((k - 2) << 4)];     // u-only: dir(u,w) = k - 2
+        else cls = c == 3u ? 2u : 1u;                       // dyadic base: 102 if mutual, else 012
+        if (v) atomicAdd(&s[cls], v);
+    }
+    const unsigned long long h = hist[t];
+    if (h) {
+        const uint32_t cab = t & 3u;                                   // tricode bits of the pair (a, b)
+        const uint32_t dac = (t >> 4) & 3u;                            // dir(a,c) seen from a
+        const uint32_t dbc = (t >> 2) & 3u;                            // dir(b,c) seen from b
+        const uint32_t dcb = ((dbc & 1u) << 1) | (dbc >> 1);           // dir(c,b) seen from c
+        const uint32_t cac = ((dac & 1u) << 1) | (dac >> 1);           // tricode bits of the pair (a, c)
+        const unsigned long long m = 0ull - h;
+        atomicAdd(&s[T.t[t]], h);                                      // the triad, at (a, b) with w = c
+        atomicAdd(&s[T.t[cab | (dac << 4)]], m);                       // c is no u-only vertex of (a, b)
+        atomicAdd(&s[T.t[cab | (dbc << 2)]], m);                       // nor a v-only one
+        atomicAdd(&s[T.t[cac | (dcb << 2)]], m);                       // b is no v-only vertex of (a, c)
+        atomicAdd(&s[cab == 3u ? 2u : 1u], h);                         // a common neighbour of each pair
+        atomicAdd(&s[dac == 3u ? 2u : 1u], h);
+        atomicAdd(&s[dbc == 3u ? 2u : 1u], h);
+    }
+    __syncthreads();
+    if (t >= 1 && t < 16 && s[t]) atomicAdd(&out16[t], s[t]);
+}
+
+std::atomic<uint64_t> g_tri_attr[2] = {};
+
+size_t tri_smem(uint32_t chunk, bool old) {
+    const size_t slots = 2ull * chunk;
+    return sizeof(uint32_t) * (slots * (old ? 2 : 1) + (size_t)kWarps * kWarpSlots * (old ? 2 : 1) + kWarps * 64) +
+           (old ? 9 * 64 : 0);
+}
+
+tc_status tri_prepare(bool old, size_t smem) {
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    const uint64_t bit = 1ull << (dev & 63);
+    const void* fn = old ? (const void*)k_triangles<true> : (const void*)k_triangles<false>;
+    int optin = 0;
+    TC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    TC_CUDA(cudaFuncGetAttributes(&fa, fn));
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    if ((int)smem > lim) return fail(TC_ERR_ARG, "chunk_entries too large for this GPU's shared memory");
+    if (!(g_tri_attr[old ? 1 : 0].load() & bit)) {
+        TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        g_tri_attr[old ? 1 : 0].fetch_or(bit);
+    }
+    return TC_OK;
+}
+
+}  // namespace
+
+tc_status triangles_launch(const GraphDev& gd, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
+                           uint32_t warp_end, uint32_t* ctr, const uint32_t* old, const uint8_t* d_perm_state,
+                           unsigned long long* d_hist64, unsigned long long* d_vcost, cudaStream_t st) {
+    const bool is_old = old != nullptr;
+    const size_t smem = tri_smem(o.chunk, is_old);
+    TC_TRY(tri_prepare(is_old, smem));
+    TriParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.g = gd;
+    P.items = items;
+    P.n_items = n_items;
+    P.warp_begin = warp_begin;
+    P.warp_end = warp_end;
+    P.wshift = warp_block_shift(warp_end - warp_begin, (unsigned)census_grid(o));
+    P.chunk = o.chunk;
+    P.ctr = ctr;
+    P.old = old;
+    P.perm_state = d_perm_state;
+    P.hist = d_hist64;
+    P.vcost = d_vcost;
+    const unsigned grid = (unsigned)census_grid(o);
+    if (is_old) k_triangles<true><<<grid, kThreads, smem, st>>>(P);
+    else k_triangles<false><<<grid, kThreads, smem, st>>>(P);
+    TC_LAUNCH("k_triangles");
+    return TC_OK;
+}
+
+tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items,
+                                  uint32_t warp_begin, uint32_t warp_end, uint32_t bulk_v0, uint32_t bulk_v1,
+                                  cudaStream_t st, unsigned long long* d_out16, unsigned long long* d_vcost) {
+    if (g.e_sym == 0) return TC_OK;
+    if (!g.vs.p) return fail(TC_ERR_ARG, "the triangle form needs the per upper pair tables");
+    if (!g.tri.p) TC_TRY(g.tri.alloc_persistent(sizeof(unsigned long long) * 96));
+    unsigned long long* raw = g.tri.as<unsigned long long>();   // [0, 21) bulk sums, [32, 96) triangle tricodes
+    unsigned long long* hist = raw + 32;
+    TC_CUDA(cudaMemsetAsync(raw, 0, sizeof(unsigned long long) * 96, st));
+    TC_CUDA(cudaMemsetAsync(g.ctr.p, 0, sizeof(uint32_t) * 4, st));
+    const GraphDev gd = g.dev();
+    if (bulk_v1 > bulk_v0) {
+        k_pair_bulk<<<grid_for((uint64_t)(bulk_v1 - bulk_v0) * 32, 256, 8u * (unsigned)sm_count()), 256, 0, st>>>(
+            gd, bulk_v0, bulk_v1, raw);
+        TC_LAUNCH("k_pair_bulk");
+    }
+    TC_TRY(triangles_launch(gd, o, items, n_items, warp_begin, warp_end, g.ctr.as<uint32_t>(), nullptr, nullptr, hist,
+                            d_vcost, st));
+    Table64 T;
+    const uint8_t* ht = host_tricode_table();
+    if (!ht) return fail(TC_ERR_ARG, "tricode table derivation failed");
+    std::memcpy(T.t, ht, 64);
+    k_tri_fold<<<1, 64, 0, st>>>(raw, hist, T, d_out16);
+    TC_LAUNCH("k_tri_fold");
+    return TC_OK;
+}
+
+}  // namespace tc

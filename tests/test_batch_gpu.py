@@ -73,6 +73,14 @@ def test_autotuned_plan_is_exact(tc, mixed):
         best, ms = tc.tc_batch_autotune(b, max_trials=6)
         assert ms > 0 and best["chunk_entries"] >= 512
         assert tc.tc_batch_census(b, len(gs)) == want
+        # the whole coordinate descent: the default first, every trial timed, the best kept
+        best, ms = tc.tc_batch_autotune(b)
+        hist = tc.tc_batch_autotune_history(b)
+        assert len(hist) > 6 and all(t > 0 for _, t in hist)
+        assert ms == min(t for _, t in hist) and hist[0][1] >= ms
+        assert {o["algo"] for o, _ in hist} == {0, 1}
+        assert {o["ctas_per_sm"] for o, _ in hist} >= {2, 3, 4}
+        assert tc.tc_batch_census(b, len(gs)) == want
     finally:
         tc.tc_batch_destroy(b)
 

@@ -13,7 +13,7 @@ from census_facts import REVERSE, check_invariants, choose2, choose3, permute_cl
 
 pytestmark = pytest.mark.gpu
 
-ALGOS = [{"algo": 0}, {"algo": 1}]
+ALGOS = [{"algo": 0}, {"algo": 1}, {"algo": 2}]
 TIERS = [
     {},                                                       # defaults: warp <= 64, chunk 2048 / 4096
     {"warp_max_deg": 8, "chunk_entries": 512, "item_work": 2048},   # tiny chunks: hubs split
@@ -73,7 +73,7 @@ def test_rmat_scale10_stats_match_oracle_cleaning(tc):
     assert info["mutual"] == inv["M"] and info["e_sym"] == inv["M"] + inv["A"]
 
 
-@pytest.mark.parametrize("algo", [0, 1])
+@pytest.mark.parametrize("algo", [0, 1, 2])
 def test_chung_lu_golden(tc, algo):
     import os
     vals = {}
@@ -91,7 +91,7 @@ def test_chung_lu_batch_members_match_oracle(tc, idx):
     i = int(np.argsort(sizes)[[0, 100, 1000, 2500, 4000, 4095][idx]])
     n, s, d = graphgen.chung_lu(int(sizes[i]), 8.0, 2.1, 0.1, 4, i)
     want = oracle.census_bm(n, s, d)
-    for algo in (0, 1):
+    for algo in (0, 1, 2):
         assert gpu_census(tc, n, s, d, {"algo": algo}) == want
 
 
@@ -103,7 +103,8 @@ def test_random_small_graphs_match_brute_force(tc, seed):
     n = int(rng.integers(3, 65))
     n, s, d = graphgen.gnp(n, float(rng.choice([0.03, 0.1, 0.3, 0.7])), seed)
     want = oracle.census_brute(n, s, d)
-    for opts in ({"algo": 0}, {"algo": 1}, {"algo": 1, "warp_max_deg": 2, "chunk_entries": 512}):
+    for opts in ({"algo": 0}, {"algo": 1}, {"algo": 1, "warp_max_deg": 2, "chunk_entries": 512}, {"algo": 2},
+                 {"algo": 2, "warp_max_deg": 2, "chunk_entries": 512}):
         assert gpu_census(tc, n, s, d, opts, device=bool(seed % 2)) == want
 
 
@@ -120,7 +121,7 @@ def test_complete_mutual_graph(tc, n):
     s, d = arcs([(a, b) for a in range(n) for b in range(n) if a != b])
     want = [0] * 16
     want[15] = choose3(n)
-    for algo in (0, 1):
+    for algo in (0, 1, 2):
         assert gpu_census(tc, n, s, d, {"algo": algo, "chunk_entries": 512, "warp_max_deg": 16}) == want
 
 
@@ -129,7 +130,7 @@ def test_transitive_tournament(tc, n):
     s, d = arcs([(a, b) for a in range(n) for b in range(a + 1, n)])
     want = [0] * 16
     want[8] = choose3(n)
-    for algo in (0, 1):
+    for algo in (0, 1, 2):
         assert gpu_census(tc, n, s, d, {"algo": algo, "chunk_entries": 512, "warp_max_deg": 16}) == want
 
 
@@ -140,7 +141,7 @@ def test_hub_star_spans_many_chunks(tc, n):
     want = [0] * 16
     want[3] = choose2(n - 1)
     want[0] = choose3(n - 1)
-    for algo in (0, 1):
+    for algo in (0, 1, 2):
         assert gpu_census(tc, n, s, d, {"algo": algo, "chunk_entries": 1024}) == want
         assert gpu_census(tc, n, d, s, {"algo": algo, "chunk_entries": 1024}) == permute_classes(want, REVERSE)
 
@@ -191,7 +192,8 @@ def test_too_many_vertices_is_an_error(tc):
 def test_bad_options_are_rejected(tc):
     n, s, d = graphgen.gnp(20, 0.2, 1)
     with tc.Graph.from_arcs(n, s, d) as g:
-        for bad in ({"chunk_entries": 1000}, {"warp_max_deg": 4096}, {"algo": 7}, {"ctas_per_sm": 50}):
+        for bad in ({"chunk_entries": 1000}, {"warp_max_deg": 4096}, {"algo": 7}, {"ctas_per_sm": 50},
+                    {"algo": 2, "warp_max_deg": 256}, {"algo": 2, "chunk_entries": 16384}):
             with pytest.raises(tc.TcError):
                 g.census(options=bad)
         with pytest.raises(tc.TcError):
@@ -296,6 +298,8 @@ def test_rmat_scale20_union_equals_suffix_and_tiers(tc, rmat20):
         assert g.census(options={"algo": 1, "chunk_entries": 1024, "warp_max_deg": 16}) == base
         assert g.census(options={"algo": 1, "map_mode": 2}) == base
         assert g.census(options={"algo": 0, "map_mode": 2}) == base
+        assert g.census(options={"algo": 2}) == base
+        assert g.census(options={"algo": 2, "chunk_entries": 512, "warp_max_deg": 16, "item_work": 4096}) == base
         inv_sum = sum(base)
     assert inv_sum == choose3(n)
 
@@ -319,7 +323,7 @@ def test_rmat_scale20_random_induced_subgraph_matches_oracle(tc, rmat20):
     keep = np.sort(np.random.default_rng(20).choice(n, 50000, replace=False))
     k, ss, dd = _induced(n, s, d, keep)
     want = oracle.census_bm(k, ss, dd)
-    for algo in (0, 1):
+    for algo in (0, 1, 2):
         assert gpu_census(tc, k, ss, dd, {"algo": algo}) == want
 
 
@@ -330,5 +334,6 @@ def test_rmat_scale20_hub_core_matches_oracle(tc, rmat20):
     keep = np.sort(np.argsort(-deg, kind="stable")[:1200])
     k, ss, dd = _induced(n, s, d, keep)
     want = oracle.census_bm(k, ss, dd)
-    for opts in ({"algo": 0}, {"algo": 1}, {"algo": 1, "chunk_entries": 512, "warp_max_deg": 4}):
+    for opts in ({"algo": 0}, {"algo": 1}, {"algo": 1, "chunk_entries": 512, "warp_max_deg": 4}, {"algo": 2},
+                 {"algo": 2, "chunk_entries": 512, "warp_max_deg": 4}):
         assert gpu_census(tc, k, ss, dd, opts) == want

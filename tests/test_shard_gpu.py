@@ -49,6 +49,8 @@ OPTS = [
     {"algo": 0},
     {"algo": 1, "warp_max_deg": 8, "chunk_entries": 512, "item_work": 2048},   # many items, chunked hubs
     {"algo": 1, "map_mode": 2},
+    {"algo": 2},
+    {"algo": 2, "warp_max_deg": 8, "chunk_entries": 512, "item_work": 2048},
 ]
 
 
