@@ -42,7 +42,6 @@ WORKLOADS = {10: dict(name="rmat10_ef16_r15_seed1", scale=10, edge_factor=16, re
              20: dict(name="rmat20_ef16_r20_seed2", scale=20, edge_factor=16, recip=0.2, seed=2),
              26: dict(name="rmat26_ef16_r20_seed3", scale=26, edge_factor=16, recip=0.2, seed=3)}
 WORKLOAD = dict(WORKLOADS[26])
-CENSUS_SRC = os.path.join(ROOT, "paper_1209_6308_gb300", "csrc", "census.cu")
 
 
 def parse(argv=None):
@@ -51,7 +50,7 @@ def parse(argv=None):
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--algo", default="suffix", choices=["suffix", "union"])
+    p.add_argument("--algo", default="triangle", choices=["triangle", "suffix", "union"])
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--learned-reps", type=int, default=3, help="censuses per arm of the learned-vs-plain timing")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -60,6 +59,7 @@ def parse(argv=None):
     p.add_argument("--autotune-trials", type=int, default=0, help="0 = the autotuner's whole search")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-schedule comparison")
     p.add_argument("--no-medium", action="store_true", help="skip the scale-20 section")
+    p.add_argument("--no-forms", action="store_true", help="skip the suffix-form timing beside the headline form")
     p.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) run")
     p.add_argument("--no-interval", action="store_true", help="skip the interval (windowed stream) census run")
     p.add_argument("--no-census64", action="store_true", help="skip the 64-state census run")
@@ -268,16 +268,20 @@ def census_code_hash(text: str) -> str:
     return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
-def traffic_file(workload_name: str) -> str:
-    return os.path.join(ROOT, "profiles", f"k_census_{workload_name.split('_')[0]}_traffic.txt")
+KERNEL_SRC = {"k_census": "census.cu", "k_triangles": "triangles.cu"}
 
 
-def stored_traffic(workload_name: str = "rmat20_ef16_r20_seed2"):
-    """Per-launch DRAM bytes of k_census on a workload from the committed ncu summary, if it was
-    taken on this census.cu code (else None)."""
+def traffic_file(workload_name: str, kernel: str = "k_census") -> str:
+    return os.path.join(ROOT, "profiles", f"{kernel}_{workload_name.split('_')[0]}_traffic.txt")
+
+
+def stored_traffic(workload_name: str = "rmat20_ef16_r20_seed2", kernel: str = "k_census"):
+    """Per-launch DRAM bytes of a kernel on a workload from the committed ncu summary, if it was
+    taken on the current code of the kernel's source file (else None)."""
     try:
-        kv = dict(line.split(":", 1) for line in open(traffic_file(workload_name)) if ":" in line)
-        if kv.get("census_code_sha256_16", "").strip() == census_code_hash(open(CENSUS_SRC).read()):
+        src = os.path.join(ROOT, "paper_1209_6308_gb300", "csrc", KERNEL_SRC[kernel])
+        kv = dict(line.split(":", 1) for line in open(traffic_file(workload_name, kernel)) if ":" in line)
+        if kv.get("code_sha256_16", kv.get("census_code_sha256_16", "")).strip() == census_code_hash(open(src).read()):
             return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         pass
@@ -343,20 +347,23 @@ def batched_comparison(tc, torch, sh, st, trials):
             "counts_identical": same_default and same_tuned}
 
 
-def learned_comparison(tc, g, stream, model, info, reps, bytes_alg):
-    """Cost model trained on R-MAT scales 18-22 (seeds 18-22) from cycles the plain census
-    measures, attached to the bench graph: census time with the plain and the learned schedule
-    (identical counts required), each arm's roofline, and the held-out cost-prediction error."""
+def learned_comparison(tc, g, stream, model, info, reps, bytes_alg, algo):
+    """Cost model trained on R-MAT scales 18-22 (seeds 18-22) from cycles the plain census of the
+    same kernel form measures, attached to the bench graph: census time with the plain and the
+    learned schedule (identical counts required), each arm's roofline, and the held-out
+    cost-prediction error."""
     from paper_1209_6308_gb300 import learned
+    plain, learn = {"algo": algo}, {"algo": algo, "schedule": tc.TC_SCHED_LEARNED}
     learned.attach(model, g, stream=stream.cuda_stream)
-    plain_ms, plain_c = learned.census_ms(g, learned.PLAIN, stream, reps=reps)
-    learned_ms, learned_c = learned.census_ms(g, learned.LEARNED, stream, reps=reps)
-    q = learned.prediction_quality(model, g, stream=stream.cuda_stream)
+    plain_ms, plain_c = learned.census_ms(g, plain, stream, reps=reps)
+    learned_ms, learned_c = learned.census_ms(g, learn, stream, reps=reps)
+    q = learned.prediction_quality(model, g, options=plain, stream=stream.cuda_stream)
     return {"_plain_counts": plain_c, "training": info, "plain_ms": plain_ms, "learned_ms": learned_ms, "reps": reps,
             "speedup": plain_ms / learned_ms, "counts_identical": plain_c == learned_c,
             "plain_arcs_per_s": None, "learned_arcs_per_s": None,
-            "roofline_plain": roofline_hbm(bytes_alg, plain_ms, "k_census (plain plan)"),
-            "roofline_learned": roofline_hbm(bytes_alg, learned_ms, "k_census (learned plan)"),
+            "roofline_plain": roofline_hbm(bytes_alg, plain_ms, f"{FORM_NAMES[algo]} form, plain plan", None, "issue"),
+            "roofline_learned": roofline_hbm(bytes_alg, learned_ms, f"{FORM_NAMES[algo]} form, learned plan", None,
+                                             "issue"),
             "heldout_rms_log_cycle_error": {"model": q["rms_log_err_model"], "degree": q["rms_log_err_degree"],
                                             "vertices": q["vertices"]}}
 
@@ -509,7 +516,7 @@ def interval_comparison(tc, torch, s, d, n, sh, name):
     t = np.sort(rng.integers(0, 1000, len(s))).astype(np.uint64)
     src, dst = s[perm], d[perm]
     times, windows = [], []
-    with tc.Stream(n, 200, options={"algo": tc.TC_ALGO_SUFFIX}, stream=sh) as st:
+    with tc.Stream(n, 200, options={"algo": tc.TC_ALGO_TRIANGLE}, stream=sh) as st:
         t0 = time.perf_counter()
         st.push(src, dst, t)
         push_s = time.perf_counter() - t0
@@ -563,24 +570,45 @@ def roofline_hbm(bytes_alg: int, ms: float, kernel: str, traffic=None, bound="hb
             "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel, "bytes_alg_per_launch": bytes_alg}
 
 
-def medium_section(tc, torch, stream, opts, steps=5):
-    """The scale-20 workload (configuration 2): census time (plain schedule), its roofline and
-    the union-walk form's time for comparison."""
+FORM_NAMES = {0: "union", 1: "suffix", 2: "triangle"}
+
+
+def form_roofline(tc, n, info, algo, ms):
+    """Roofline of one census: the scope formula's bytes, and the bytes the form itself reads."""
+    kernel = "k_triangles" if algo == tc.TC_ALGO_TRIANGLE else "k_census"
+    r = roofline_hbm(bytes_alg_8d(n, info), ms, kernel, None, "issue")
+    if algo == tc.TC_ALGO_TRIANGLE:
+        r["bytes_alg_walked"] = info["bytes_alg_tri"]
+    elif algo == tc.TC_ALGO_SUFFIX:
+        r["bytes_alg_walked"] = info["bytes_alg"]
+    if "bytes_alg_walked" in r:
+        r["achieved_walked"] = r["bytes_alg_walked"] / (ms * 1e-3) / 1e9
+        r["frac_walked"] = r["achieved_walked"] / r["peak"]
+    return r
+
+
+def medium_section(tc, torch, stream, steps=5):
+    """The scale-20 workload (configuration 2): census time of each kernel form (plain
+    schedule), with rooflines; all three must give the same counts."""
     import graphgen
     sh = stream.cuda_stream
     n, s, d = graphgen.rmat(20, 16, 0.2, 2)
     from paper_1209_6308_gb300 import learned
-    with tc.Graph.from_arcs(n, s, d, stream=sh, options=opts) as g:
+    out = {"workload": WORKLOADS[20]["name"], "n": n, "arcs": len(s)}
+    counts = {}
+    with tc.Graph.from_arcs(n, s, d, stream=sh) as g:        # created without options: the union walk by default
         info = g.stats()
-        ms, c = learned.census_ms(g, opts, stream, reps=steps)
-        ms_union, c_union = learned.census_ms(g, {"algo": tc.TC_ALGO_UNION}, stream, reps=3)
+        out["e_sym"] = info["e_sym"]
+        for algo in (tc.TC_ALGO_TRIANGLE, tc.TC_ALGO_SUFFIX, tc.TC_ALGO_UNION):
+            ms, c = learned.census_ms(g, {"algo": algo} if algo else None, stream, reps=steps if algo else 3)
+            counts[algo] = c
+            out[FORM_NAMES[algo]] = {"ms": ms, "arcs_per_s": len(s) / (ms * 1e-3),
+                                     "roofline": form_roofline(tc, n, info, algo, ms)}
+    c = counts[tc.TC_ALGO_TRIANGLE]
+    out["forms_agree"] = all(v == c for v in counts.values())
     c[0] = tc.tc_null_count(n, c)
-    c_union[0] = tc.tc_null_count(n, c_union)
-    return {"workload": WORKLOADS[20]["name"], "n": n, "arcs": len(s), "e_sym": info["e_sym"], "ms": ms,
-            "arcs_per_s": len(s) / (ms * 1e-3), "union_walk_ms": ms_union, "census": c,
-            "union_equals_suffix": c == c_union,
-            "roofline": dict(roofline_hbm(bytes_alg_8d(n, info), ms, "k_census", stored_traffic(), "issue"),
-                             bytes_alg_walked=info["bytes_alg"])}
+    out["census"] = c
+    return out
 
 
 def run_gpu(args):
@@ -594,7 +622,7 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    algo = tc.TC_ALGO_SUFFIX if args.algo == "suffix" else tc.TC_ALGO_UNION
+    algo = {"triangle": tc.TC_ALGO_TRIANGLE, "suffix": tc.TC_ALGO_SUFFIX, "union": tc.TC_ALGO_UNION}[args.algo]
     opts = {"algo": algo}
     log("generating the workload")
     t0 = time.perf_counter()
@@ -686,13 +714,24 @@ def run_gpu(args):
     if not args.no_learned:
         from paper_1209_6308_gb300 import learned
         log("training the cost model")
-        model, minfo = learned.train_cost_model(scales=(18, 19, 20, 21, 22), steps=800, stream=sh)
+        model, minfo = learned.train_cost_model(scales=(18, 19, 20, 21, 22), steps=800, stream=sh, options=opts)
         log(f"cost model trained: {minfo}")
-        learned_line = learned_comparison(tc, g, stream, model, minfo, args.learned_reps, b8d)
+        learned_line = learned_comparison(tc, g, stream, model, minfo, args.learned_reps, b8d, algo)
+        learned_line["kernel_form"] = args.algo
         learned_line["plain_arcs_per_s"] = arcs / (learned_line["plain_ms"] * 1e-3)
         learned_line["learned_arcs_per_s"] = arcs / (learned_line["learned_ms"] * 1e-3)
         learned_line["counts_identical_to_timed"] = learned_line.pop("_plain_counts")[1:] == counts[1:]
         log("learned comparison done")
+    forms_line = None
+    if not args.no_forms and algo != tc.TC_ALGO_SUFFIX:
+        from paper_1209_6308_gb300 import learned
+        log("suffix form timing")
+        ms_suf, c_suf = learned.census_ms(g, {"algo": tc.TC_ALGO_SUFFIX}, stream, reps=2)
+        forms_line = {"suffix": {"ms": ms_suf, "arcs_per_s": arcs / (ms_suf * 1e-3),
+                                 "roofline": form_roofline(tc, n, info, tc.TC_ALGO_SUFFIX, ms_suf),
+                                 "counts_equal": c_suf[1:] == counts[1:]},
+                      FORM_NAMES[algo]: {"ms": ms, "arcs_per_s": arcs / (ms * 1e-3)},
+                      "speedup": ms_suf / ms}
     g.close()
     del flush
     torch.cuda.empty_cache()
@@ -700,7 +739,7 @@ def run_gpu(args):
     medium_line = None
     if not args.no_medium and WORKLOAD["scale"] != 20:
         log("scale-20 section")
-        medium_line = medium_section(tc, torch, stream, opts)
+        medium_line = medium_section(tc, torch, stream)
     interval_line = None
     if not args.no_interval:
         log("interval census")
@@ -722,7 +761,14 @@ def run_gpu(args):
     if model is not None:
         tc.tc_costmodel_destroy(model)
 
-    traffic = stored_traffic(WORKLOAD["name"])
+    kernel = "k_triangles" if algo == tc.TC_ALGO_TRIANGLE else "k_census"
+    traffic = stored_traffic(WORKLOAD["name"], kernel)
+    roof = form_roofline(tc, n, info, algo, ms)
+    roof["traffic"] = traffic
+    roof["note"] = ("bytes_alg_per_launch = 8(n+1) + 8 E + sum over upper pairs (4 d_v + 16) + 128 (each pair "
+                    "streams N[v], the paper's walk); bytes_alg_walked = what this kernel form reads "
+                    "(tc_graph_info); the kernel is bound by load latency and instruction issue (ncu), not by "
+                    "HBM bandwidth")
     line = {
         "metric": METRIC, "value": job_value(arcs, ms),
         "unit": "arcs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -732,15 +778,12 @@ def run_gpu(args):
                    "algo": args.algo, "schedule": "plain",
                    "l2": "inputs far larger than L2 (CSR and tables); also flushed between steps (512 MB write)",
                    "parallelism": f"shard{world}" if world > 1 else "single"},
-        "roofline": dict(roofline_hbm(b8d, ms / 1.0, "k_census", traffic, "issue"),
-                         bytes_alg_walked=info["bytes_alg"],
-                         note="bytes_alg_per_launch = 8(n+1) + 8 E + sum over upper pairs (4 d_v + 16) + 128; "
-                              "bytes_alg_walked = the N[v] entries the census actually walks (tc_graph_info); "
-                              "the kernel is instruction-issue bound (ncu), not HBM bound"),
+        "roofline": roof,
         "e2e": ({"value": job_value(arcs, e2e_job_ms), "unit": "arcs/s",
                  "h2d_bytes_per_step": 8 * arcs, "d2h_bytes_per_step": 16 * 16,
                  "ms_per_step": e2e_job_ms} if e2e_ms else None),
-        "gpu_launches": args.steps,
+        # per census: k_pair_bulk, k_triangles, k_tri_fold (triangle form) or k_census
+        "gpu_launches": args.steps * (3 if algo == tc.TC_ALGO_TRIANGLE else 1),
         "clocks": clk.summary(),
         "census": counts,
         "census_e2e_equal": (e2e_counts == counts) if e2e_counts else None,
@@ -749,6 +792,8 @@ def run_gpu(args):
     }
     if learned_line is not None:
         line["learned"] = learned_line
+    if forms_line is not None:
+        line["forms"] = forms_line
     if medium_line is not None:
         line["medium"] = medium_line
     if interval_line is not None:

@@ -103,10 +103,18 @@ typedef struct {
     uint64_t sum_walk;        /* sum over upper pairs u<v of |{w in N(v): w > u}|: the N[v] entries
                                  a census walks */
     uint64_t sum_walk_map;    /* those of them with ids below 2^17 (answered by the direct id map) */
+    uint64_t sum_tri_walk;    /* sum over upper pairs (b, c) of the neighbours of c with (relabelled) ids
+                                 below b: the entries TC_ALGO_TRIANGLE walks */
+    uint64_t bytes_alg_tri;   /* algorithmic bytes of one TC_ALGO_TRIANGLE census (below) */
 } tc_graph_info;
 /* bytes_alg = 16(n+1) + 44 e_sym + 4 sum_walk + 128: the CSR read once (offsets 8(n+1), lists
  * 8 e_sym), the per-pair tables (8(n+1) + 20 e_sym), 16 B of bookkeeping per pair, 4 B per
- * N[v] entry walked, and the 16 counters. */
+ * N[v] entry walked, and the 16 counters.
+ * bytes_alg_tri = 32(n+1) + 60 e_sym + 4 sum_tri_walk + 1280: per vertex 32 B (offsets, lower-
+ * neighbour counts and table starts, read by the bulk pass and by the walk); per upper pair
+ * 60 B (the bulk pass: the pair's entry, its 20 B of tables and the other end's two offsets;
+ * the walk: the entry again, the other end's offset, the pair's position table entry, and the
+ * pair's share of the staged lower lists); 4 B per entry walked; the 96 counters and the fold. */
 
 /* Build a graph from an arc list (Sec. 6, Fig. 7).  src[i] -> dst[i] for i < m; self-loops
  * and repeated arcs are dropped and counted.  Ids >= n give TC_ERR_RANGE.  src/dst are

@@ -52,6 +52,7 @@ def _load():
         lib.or_census_bm_parallel.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p, ctypes.c_int]
         lib.or_census_brute.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p]
         lib.or_invariants.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p]
+        lib.or_invariants_opt.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p, ctypes.c_int]
         lib.or_census64_brute.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p]
         lib.or_census64.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u32p, u32p, u64p]
         lib.or_graph_new.restype = ctypes.c_void_p
@@ -157,10 +158,11 @@ def fold64(c64) -> list:
     return out
 
 
-def invariants(n: int, src, dst) -> dict:
+def invariants(n: int, src, dst, triangles: bool = True) -> dict:
+    """O(m) statistics of the digraph; triangles=False skips the triangle count (reported 0)."""
     s, d, ps, pd = _arcs(src, dst)
     out = np.zeros(16, dtype=np.uint64)
-    if _load().or_invariants(n, len(s), ps, pd, _p64(out)) != 0:
+    if _load().or_invariants_opt(n, len(s), ps, pd, _p64(out), int(triangles)) != 0:
         raise ValueError("vertex id out of range")
     v = _u128(out, 8)
     return dict(zip(("M", "A", "N", "out2", "in2", "paths", "triangles", "arcs"), v))

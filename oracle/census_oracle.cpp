@@ -592,7 +592,10 @@ int or_census_brute(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t*
 //   0 mutual dyads M, 1 asymmetric dyads A, 2 null dyads C(n,2)-M-A,
 //   3 sum_v C(dout,2), 4 sum_v C(din,2), 5 sum_v (din*dout - mutual partners of v),
 //   6 undirected triangles, 7 distinct arcs.
-int or_invariants(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst, uint64_t* out) {
+// The O(m) statistics; with_triangles = 0 leaves the triangle count (the one superlinear part)
+// at 0, for graphs too large to count them on the CPU.
+int or_invariants_opt(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst, uint64_t* out,
+                      int with_triangles) {
     Digraph g;
     if (!build_digraph(n, m, src, dst, g)) return -1;
     u128 M = 0, A = 0, out2 = 0, in2 = 0, paths = 0, tri = 0;
@@ -611,16 +614,16 @@ int or_invariants(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* d
     }
     // triangles, each once: orient every pair from lower to higher (degree, id) rank and
     // count, for each oriented pair a->b, the common out-neighbours of a and b
-    std::vector<uint64_t> deg(n);
-    for (uint32_t x = 0; x < n; ++x) deg[x] = g.N[x].size();
+    std::vector<uint64_t> deg(with_triangles ? n : 0);
+    for (uint32_t x = 0; x < deg.size(); ++x) deg[x] = g.N[x].size();
     auto before = [&](uint32_t x, uint32_t y) { return deg[x] < deg[y] || (deg[x] == deg[y] && x < y); };
-    std::vector<std::vector<uint32_t>> fwd(n);
-    for (uint32_t x = 0; x < n; ++x) {
+    std::vector<std::vector<uint32_t>> fwd(with_triangles ? n : 0);
+    for (uint32_t x = 0; x < fwd.size(); ++x) {
         for (const Tagged& t : g.N[x])
             if (before(x, t.id)) fwd[x].push_back(t.id);
         std::sort(fwd[x].begin(), fwd[x].end());
     }
-    for (uint32_t a = 0; a < n; ++a)
+    for (uint32_t a = 0; a < fwd.size(); ++a)
         for (uint32_t b : fwd[a]) {
             auto ia = fwd[a].begin(), ib = fwd[b].begin();
             while (ia != fwd[a].end() && ib != fwd[b].end()) {
@@ -631,6 +634,10 @@ int or_invariants(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* d
     u128 vals[8] = {M, A, pairs - M - A, out2, in2, paths, tri, (u128)g.arcs};
     for (int k = 0; k < 8; ++k) { out[2 * k] = (uint64_t)vals[k]; out[2 * k + 1] = (uint64_t)(vals[k] >> 64); }
     return 0;
+}
+
+int or_invariants(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst, uint64_t* out) {
+    return or_invariants_opt(n, m, src, dst, out, 1);
 }
 
 }  // extern "C"

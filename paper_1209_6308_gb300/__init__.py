@@ -52,7 +52,8 @@ class tc_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("max_deg", ctypes.c_uint32), ("arcs", ctypes.c_uint64),
                 ("e_sym", ctypes.c_uint64), ("mutual", ctypes.c_uint64), ("loops_dropped", ctypes.c_uint64),
                 ("dups_dropped", ctypes.c_uint64), ("sum_d2", ctypes.c_uint64), ("sum_dv_upper", ctypes.c_uint64),
-                ("bytes_alg", ctypes.c_uint64), ("sum_walk", ctypes.c_uint64), ("sum_walk_map", ctypes.c_uint64)]
+                ("bytes_alg", ctypes.c_uint64), ("sum_walk", ctypes.c_uint64), ("sum_walk_map", ctypes.c_uint64),
+                ("sum_tri_walk", ctypes.c_uint64), ("bytes_alg_tri", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -315,6 +315,8 @@ tc_status tc_graph_stats(const tc_graph* g, tc_graph_info* info) {
     info->sum_dv_upper = s.sum_dv_upper;
     info->sum_walk = s.sum_walk;
     info->sum_walk_map = s.sum_walk_map;
+    info->sum_tri_walk = s.sum_tri_walk;
+    info->bytes_alg_tri = 32ull * (s.n + 1ull) + 60ull * s.e_sym + 4ull * s.sum_tri_walk + 1280ull;
     info->bytes_alg = 16ull * (s.n + 1ull) + 44ull * s.e_sym + 4ull * s.sum_walk + 128ull;
     return TC_OK;
 }

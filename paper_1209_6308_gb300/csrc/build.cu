@@ -126,10 +126,11 @@ __global__ void k_up(const uint64_t* off, const uint32_t* adj, uint32_t n, uint3
 }
 
 // stats[3] sum deg^2, stats[4] sum over upper pairs of deg(v), stats[5] max degree,
-// stats[7] vertices with deg > 0
+// stats[7] vertices with deg > 0, stats[10] sum of up (up - 1) / 2 (the entries the triangle form
+// walks: for every upper pair (b, c), the neighbours of c below b)
 __global__ void k_graph_sums(const uint64_t* off, const uint32_t* adj, const uint32_t* up, uint32_t n,
                              unsigned long long* stats) {
-    unsigned long long d2 = 0, dv = 0;
+    unsigned long long d2 = 0, dv = 0, tw = 0;
     uint32_t mx = 0, act = 0;
     for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t d = off[x + 1] - off[x];
@@ -138,10 +139,12 @@ __global__ void k_graph_sums(const uint64_t* off, const uint32_t* adj, const uin
         act += (d > 0);
         // x is the v of every pair (u, x) with u < x: the first up[x] neighbours
         dv += (unsigned long long)up[x] * d;
+        tw += (unsigned long long)up[x] * (up[x] ? up[x] - 1ull : 0ull) / 2ull;
     }
     for (int o = 16; o; o >>= 1) {
         d2 += __shfl_xor_sync(0xffffffffu, d2, o);
         dv += __shfl_xor_sync(0xffffffffu, dv, o);
+        tw += __shfl_xor_sync(0xffffffffu, tw, o);
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         act += __shfl_xor_sync(0xffffffffu, act, o);
     }
@@ -149,6 +152,7 @@ __global__ void k_graph_sums(const uint64_t* off, const uint32_t* adj, const uin
         if (act) atomicAdd(&stats[7], (unsigned long long)act);
         atomicAdd(&stats[3], d2);
         atomicAdd(&stats[4], dv);
+        atomicAdd(&stats[10], tw);
         atomicMax(&stats[5], (unsigned long long)mx);
     }
 }
@@ -434,9 +438,10 @@ tc_status finish_graph(GraphStore& g, uint64_t E, int B, uint64_t* ukey, uint32_
             TC_LAUNCH("k_pair_tables_long");
         }
     }
-    unsigned long long hs[10];
+    unsigned long long hs[11];
     TC_CUDA(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
     TC_CUDA(cudaStreamSynchronize(st));
+    g.sum_tri_walk = hs[10];
     g.sum_walk = hs[8];
     g.sum_walk_map = hs[9];
     g.e_sym = E;
@@ -458,8 +463,8 @@ tc_status build_from_arcs(GraphStore& g, uint64_t m, const uint32_t* d_src, cons
     const int B = bits_for(n);
     if (m >= (1ull << 32)) return fail(TC_ERR_RANGE, "more than 2^32-1 arcs");
     DevBuf stats, keys, tmp;
-    TC_TRY(stats.alloc(sizeof(unsigned long long) * 10, st));
-    TC_CUDA(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * 10, st));
+    TC_TRY(stats.alloc(sizeof(unsigned long long) * 11, st));
+    TC_CUDA(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * 11, st));
     TC_TRY(keys.alloc(sizeof(uint64_t) * (m ? m : 1), st));
     TC_TRY(tmp.alloc(sizeof(uint64_t) * (m ? m : 1), st));
     if (m) {
@@ -523,8 +528,8 @@ tc_status build_from_csr(GraphStore& g, const uint64_t* d_off, const uint32_t* d
     if (total_h & 1) return fail(TC_ERR_ARG, "CSR is not symmetric (odd number of entries)");
     if (total_h >= (1ull << 32)) return fail(TC_ERR_RANGE, "more than 2^32-1 CSR entries");
     DevBuf stats;
-    TC_TRY(stats.alloc(sizeof(unsigned long long) * 10, st));
-    TC_CUDA(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * 10, st));
+    TC_TRY(stats.alloc(sizeof(unsigned long long) * 11, st));
+    TC_CUDA(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * 11, st));
     const unsigned gridN = grid_for(n, kB, 1u << 16);
     k_check_csr<<<gridN, kB, 0, st>>>(d_off, d_adj, n, total_h, stats.as<unsigned long long>());
     TC_LAUNCH("k_check_csr");

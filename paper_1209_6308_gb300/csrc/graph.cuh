@@ -59,6 +59,7 @@ struct GraphStore {
     uint32_t n = 0, n_active = 0, max_deg = 0;
     uint64_t arcs = 0, e_sym = 0, mutual = 0, loops = 0, dups = 0, sum_d2 = 0, sum_dv_upper = 0, sum_walk = 0;
     uint64_t sum_walk_map = 0;   // walked entries with ids below kMapIdsSuffix
+    uint64_t sum_tri_walk = 0;   // sum of up (up - 1) / 2: the entries the triangle form walks
     DevBuf off, adj, up, new_of_old;
     DevBuf ub, rp, vs, us;   // per upper pair tables (see GraphDev)
     DevBuf ctr;        // census work counters (uint32 x 4)

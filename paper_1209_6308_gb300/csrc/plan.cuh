@@ -20,7 +20,8 @@ namespace tc {
 __device__ __forceinline__ uint64_t pair_units(const GraphDev& g, uint32_t u, uint64_t ubase, uint32_t du, uint32_t upu,
                                                uint32_t j, uint32_t chunks, int algo) {
     const uint32_t v = g.adj[ubase + j] >> 2;
-    if (algo == TC_ALGO_TRIANGLE) return (uint64_t)g.up[v] + 32ull;   // the walk of L(v) and the pair's overhead
+    // the triangle form walks the entries of N[v] below u (rp = u's position in N[v]) and a pair overhead
+    if (algo == TC_ALGO_TRIANGLE) return (uint64_t)g.rp[g.ub[u] + (j - upu)] + 32ull;
     const uint64_t dv = g.off[v + 1] - g.off[v];
     const uint64_t walk = g.rp ? dv - 1 - g.rp[g.ub[u] + (j - upu)] : dv;
     return walk + 16ull + 16ull * chunks + (algo == TC_ALGO_UNION ? du / 2 : 0ull);

@@ -8,7 +8,9 @@
 // each pair's common neighbours by walking N[v] past u.  Here each common neighbour is found
 // once, as a triangle: with ids in descending degree, L(x) = the neighbours of x with smaller
 // ids (a prefix of N[x]) is short for every x, and the triangle a < b < c is met exactly
-// once, when the walk of L(c) for the pair (b, c) finds a in L(b), staged in shared memory.
+// once, when the walk of the entries of N[c] below b (a prefix of L(c), its length the pair
+// table's position of b in N[c]) for the pair (b, c) finds a in L(b), staged in shared memory
+// (a hash, or a direct map of two direction bits per id when b's id is small).
 // Its tricode (roles (a, b, c)) then gives every correction it makes to the pairs' bulk
 // counts (Fig. 5 steps 2.1.2 - 2.1.4):
 //   + the triad itself, counted once at the pair (a, b) with w = c > b (step 2.1.4's rule);
@@ -62,16 +64,19 @@ struct TriParams {
     unsigned long long* vcost;    // optional [n]: SM cycles per CTA-tier vertex b
 };
 
-// Walk the lists L(c) of the pairs (b, c = N[b][j]), j in [j0, j1), 32 pairs per batch, and
-// count each a of L(c) found in the staged hash of L(b).  One warp; the lanes share each
-// batch's flattened (pair, position) range.  Returns the entries walked (warp-uniform).
-template <bool OLD>
-__device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, uint64_t bbase, uint32_t j0, uint32_t j1,
-                                               const uint32_t* sH, const uint32_t* sO, int hb, uint32_t hmask,
-                                               uint32_t ob, const uint8_t* sPerm, uint32_t* myHist, int lane) {
+// Walk, for the pairs (b, c = N[b][j]), j in [j0, j1), 32 pairs per batch, the entries of N[c]
+// below b (rp = b's position in N[c], from the pair tables; pb + j indexes the pair) and count
+// each a found in the staged L(b).  MAP: L(b) is a direct map of two direction bits per id (every
+// a < b is in its range); else a hash.  One warp; the lanes share each batch's flattened (pair,
+// position) range.  Returns the entries walked (warp-uniform).
+template <bool OLD, bool MAP>
+__device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, uint64_t bbase, uint64_t pb, uint32_t j0,
+                                               uint32_t j1, const uint32_t* sH, const uint32_t* sO, int hb,
+                                               uint32_t hmask, uint32_t ob, const uint8_t* sPerm, uint32_t* myHist,
+                                               int lane) {
     const uint64_t* __restrict__ off = P.g.off;
     const uint32_t* __restrict__ adj = P.g.adj;
-    const uint32_t* __restrict__ up = P.g.up;
+    const uint32_t* __restrict__ rp = P.g.rp;
     const uint32_t le_mask = (2u << lane) - 1u;
     uint32_t walked = 0;
     for (uint32_t jb = j0; jb < j1; jb += 32) {
@@ -80,7 +85,7 @@ __device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, uint64_t bbas
         uint32_t e_bc = ok ? adj[bbase + j] : 0u;
         const uint32_t c = e_bc >> 2;
         uint64_t cb = ok ? off[c] : 0ull;
-        uint32_t len = ok ? up[c] : 0u;
+        uint32_t len = ok ? rp[pb + j] : 0u;
         uint32_t oc = (OLD && ok) ? P.old[c] : 0u;
         // compact the pairs with a non-empty L(c) into lanes 0 .. cnt-1
         const uint32_t nz = __ballot_sync(0xffffffffu, len != 0u);
@@ -131,16 +136,24 @@ __device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, uint64_t bbas
                 const uint32_t e_ca = r ? xB : xA;
                 if (!e_ca) continue;
                 const uint32_t a = e_ca >> 2;
-                uint32_t h = tri_hash(a, hb);
-                uint32_t e = sH[h];
-                while (e != 0u && (e >> 2) != a) {
-                    h = (h + 1u) & hmask;
+                uint32_t e, oa = 0;
+                if (MAP) {
+                    const uint32_t dir = (sH[a >> 4] >> ((a & 15u) << 1)) & 3u;
+                    e = dir ? ((a << 2) | dir) : 0u;
+                    if (OLD && dir) oa = P.old[a];
+                } else {
+                    uint32_t h = tri_hash(a, hb);
                     e = sH[h];
+                    while (e != 0u && (e >> 2) != a) {
+                        h = (h + 1u) & hmask;
+                        e = sH[h];
+                    }
+                    if (OLD && e) oa = sO[h];
                 }
                 if (e != 0u) {
                     uint32_t t = tri_code(e, r ? EB : EA, e_ca);
                     if (OLD) {
-                        const uint32_t oa = sO[h], oc2 = r ? OB : OA;
+                        const uint32_t oc2 = r ? OB : OA;
                         const uint32_t ra = (oa > ob) + (oa > oc2), rb = (ob > oa) + (ob > oc2);
                         t = sPerm[(3u * ra + rb) * 64u + t];
                     }
@@ -185,6 +198,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
     const uint32_t* __restrict__ adj = P.g.adj;
     const uint32_t* __restrict__ up = P.g.up;
     uint32_t since_flush = 0;   // warp-uniform: entries walked since this warp's bins were flushed
+    // the hash region (2 x chunk words) holds a direct map of 32 x chunk ids at two bits each
+    const uint32_t map_ids = 32u * P.chunk;
 
     // ---------------------------------------------------------------- CTA items
     for (;;) {
@@ -198,8 +213,33 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
         const uint64_t bbase = off[b];
         const uint32_t lb = up[b];
         const uint32_t ob = OLD ? P.old[b] : 0u;
-        // L(b) = N[b][0, lb), staged `chunk` entries per pass; every pass walks the item's pairs
-        for (uint32_t c0 = 0; c0 < lb; c0 += P.chunk) {
+        const uint64_t pb = P.g.ub[b] - lb;   // table index of the pair (b, N[b][j]) is pb + j
+        if (b <= map_ids) {
+            // L(b) as a direct map of two direction bits per id below b: one pass, no probing
+            for (uint32_t k = tid; k < map_ids / 16u; k += kThreads) sH[k] = 0u;
+            if (tid == 0) s_next = w.j0;
+            __syncthreads();
+            for (uint32_t k = tid; k < lb; k += kThreads) {
+                const uint32_t e = adj[bbase + k], a = e >> 2;
+                atomicOr(&sH[a >> 4], (e & 3u) << ((a & 15u) << 1));
+            }
+            __syncthreads();
+            for (;;) {
+                uint32_t jb = 0;
+                if (lane == 0) jb = atomicAdd(&s_next, 32u);
+                jb = __shfl_sync(0xffffffffu, jb, 0);
+                if (jb >= w.j1) break;
+                since_flush += walk_pairs<OLD, true>(P, bbase, pb, jb, min(jb + 32u, w.j1), sH, nullptr, 0, 0u, ob,
+                                                     sPerm, myHist, lane);
+                if (since_flush >= kFlushElems) {
+                    flush_warp_hist(myHist, P.hist, lane);
+                    since_flush = 0;
+                }
+            }
+            __syncthreads();
+        }
+        // L(b) = N[b][0, lb), staged `chunk` entries per pass in a hash; every pass walks the item's pairs
+        for (uint32_t c0 = 0; b > map_ids && c0 < lb; c0 += P.chunk) {
             const uint32_t LA = min(P.chunk, lb - c0);
             int hb = 6;
             while ((1u << hb) < 2u * LA) ++hb;
@@ -219,8 +259,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
                 if (lane == 0) jb = atomicAdd(&s_next, 32u);
                 jb = __shfl_sync(0xffffffffu, jb, 0);
                 if (jb >= w.j1) break;
-                since_flush += walk_pairs<OLD>(P, bbase, jb, min(jb + 32u, w.j1), sH, sO, hb, hmask, ob, sPerm, myHist,
-                                               lane);
+                since_flush += walk_pairs<OLD, false>(P, bbase, pb, jb, min(jb + 32u, w.j1), sH, sO, hb, hmask, ob,
+                                                      sPerm, myHist, lane);
                 if (since_flush >= kFlushElems) {
                     flush_warp_hist(myHist, P.hist, lane);
                     since_flush = 0;
@@ -258,8 +298,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
                 if (OLD) wO[h] = P.old[e >> 2];
             }
             __syncwarp();
-            since_flush += walk_pairs<OLD>(P, bbase, lb, db, wH, wO, hb, hmask, OLD ? P.old[b] : 0u, sPerm, myHist,
-                                           lane);
+            since_flush += walk_pairs<OLD, false>(P, bbase, P.g.ub[b] - lb, lb, db, wH, wO, hb, hmask,
+                                                  OLD ? P.old[b] : 0u, sPerm, myHist, lane);
             if (since_flush >= kFlushElems) {
                 flush_warp_hist(myHist, P.hist, lane);
                 since_flush = 0;

@@ -46,6 +46,40 @@ def test_loops_duplicates_and_isolated_vertices(tc):
     assert empty[0] == 120 and sum(empty) == 120
 
 
+@pytest.mark.parametrize("which", ["chunglu600", "rmat9", "star_and_clique", "tournament400"])
+def test_skewed_graphs_equal_the_definition(tc, which):
+    """By definition (every a < b < c) on the largest graphs the brute force covers quickly,
+    chosen skewed so that hubs become CTA work items of the triangle walk (degree above 64)
+    next to warp-tier vertices."""
+    if which == "chunglu600":
+        n, s, d = graphgen.chung_lu(600, 10.0, 2.1, 0.3, 7, 1)
+    elif which == "rmat9":
+        n, s, d = graphgen.rmat(9, 16, 0.25, 11)
+    elif which == "star_and_clique":
+        # a hub linked to everything one way or both, and a dense mutual block in the middle
+        n = 500
+        pairs = [(0, x) for x in range(1, n, 2)] + [(x, 0) for x in range(2, n, 3)]
+        pairs += [(a, b) for a in range(200, 260) for b in range(200, 260) if a != b and (a * 7 + b) % 3]
+        s = np.array([p[0] for p in pairs], np.uint32)
+        d = np.array([p[1] for p in pairs], np.uint32)
+    else:
+        # a random tournament with a tenth of its pairs made mutual: every pair linked
+        n = 400
+        rng = np.random.default_rng(3)
+        a, b = np.triu_indices(n, 1)
+        flip = rng.random(len(a)) < 0.5
+        both = rng.random(len(a)) < 0.1
+        s0, d0 = np.where(flip, b, a), np.where(flip, a, b)
+        s = np.concatenate([s0, d0[both]]).astype(np.uint32)
+        d = np.concatenate([d0, s0[both]]).astype(np.uint32)
+    want = oracle.census64_brute(n, s, d)
+    with tc.Graph.from_arcs(n, s, d) as g:
+        st = g.stats()
+        got = g.census64()
+    assert st["max_deg"] > 64
+    assert got == want
+
+
 def test_larger_graphs_equal_the_pair_route(tc):
     for n, s, d in (graphgen.rmat(10, 16, 0.15, 1), graphgen.chung_lu(5000, 12.0, 2.1, 0.1, 5, 4),
                     graphgen.rmat(13, 16, 0.2, 6)):

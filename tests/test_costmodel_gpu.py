@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 import graphgen
+import oracle
 from oracle import costmodel_ref as ref
 
 pytestmark = pytest.mark.gpu
@@ -104,11 +105,12 @@ def test_learned_schedule_is_exact_and_predicts_cost_better(tc):
     model, info = learned.train_cost_model(scales=(14, 15, 16), seeds=(41, 42, 43), steps=400)
     try:
         assert info["samples"] > 100 and info["loss_final"] < info["loss_initial"]
-        n, s, d = graphgen.rmat(16, 16, 0.2, 77)               # held-out graph
+        n, s, d = graphgen.rmat(15, 16, 0.2, 77)               # held-out graph
+        want = oracle.census_bm_parallel(n, s, d)              # the oracle, not the plain GPU schedule
         with tc.Graph.from_arcs(n, s, d, options=learned.PLAIN) as g:
-            plain = g.census(options=learned.PLAIN)
             learned.attach(model, g)
-            assert g.census(options=learned.LEARNED) == plain
+            assert g.census(options=learned.LEARNED) == want
+            assert g.census(options=dict(learned.LEARNED, chunk_entries=512, item_work=4096)) == want
             q = learned.prediction_quality(model, g)
         assert q["vertices"] > 50
         assert q["rms_log_err_model"] < q["rms_log_err_degree"], q
