@@ -192,6 +192,17 @@ tc_u128 tc_null_count(uint32_t n, const uint64_t counts16[16]);
  * (the graph is in use by another call), TC_ERR_OOM, TC_ERR_CUDA. */
 tc_status tc_census64(tc_graph* g, void* stream, tc_u128 out[64]);
 
+/* The census by its matrix form (Sec. 4 names Moody's matrix census as the dense alternative to
+ * Fig. 5): with S the one-way arcs, M the mutual and N the null dyads as 0/1 matrices, each class
+ * count is a sum of an elementwise product of one of them with one of the products NN, S'S, SS',
+ * SS, NM, MM, divided by the class's symmetries (003 = sum(N o NN)/6, 012 = sum(S o NN), ...,
+ * 300 = sum(M o MM)/6).  All 16 counts come from their own sums (the null count too).  The
+ * matrices are bit-packed and each product's masked sums are fused into its tiles: O(n^3 / 64)
+ * work, a dense cross-check of the Fig. 5 kernels for graphs of n <= 2^14 vertices (larger n:
+ * TC_ERR_RANGE).  out: 16 host tc_u128.  Synchronises the stream.  TC_ERR_BUSY if the graph is
+ * in use by another call, TC_ERR_OOM, TC_ERR_CUDA. */
+tc_status tc_census_matrix(tc_graph* g, void* stream, tc_u128 out[16]);
+
 /* Census of k graphs in one persistent launch (builds a tc_batch, runs it once, frees it).
  * out16xk receives 16 uint64 per graph in the callers' order (index 0 set to the low 64 bits
  * of the null count); out003_k (may be NULL) receives each full 128-bit null count.  Host

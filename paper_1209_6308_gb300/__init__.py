@@ -114,6 +114,7 @@ SIGNATURES = {
     "tc_census_csr_noalloc": (ctypes.c_int, [_U32, _VP, _VP, _VP, _VP]),
     "tc_null_count": (tc_u128, [_U32, ctypes.POINTER(_U64)]),
     "tc_census64": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(tc_u128)]),
+    "tc_census_matrix": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(tc_u128)]),
     "tc_census_batch": (ctypes.c_int, [_VP, _U32, _VP, ctypes.POINTER(_U64), ctypes.POINTER(tc_u128)]),
     "tc_batch_create": (ctypes.c_int, [_VP, _U32, _VP, _VP, ctypes.POINTER(_VP)]),
     "tc_batch_census_async": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -261,6 +262,14 @@ def tc_census64(g: int, stream=None) -> list:
     out = (tc_u128 * 64)()
     _check(load().tc_census64(g, _stream_handle(stream), out), "tc_census64")
     return [out[i].value() for i in range(64)]
+
+
+def tc_census_matrix(g: int, stream=None) -> list:
+    """The census by its matrix form (Sec. 4): 16 class counts from masked sums of products of
+    the bit-packed one-way, mutual and null dyad matrices (n <= 2^14; synchronises the stream)."""
+    out = (tc_u128 * 16)()
+    _check(load().tc_census_matrix(g, _stream_handle(stream), out), "tc_census_matrix")
+    return [out[i].value() for i in range(16)]
 
 
 def tc_census(g: int, stream=None, options=None) -> list:
@@ -729,6 +738,9 @@ class Graph:
 
     def census64(self, stream=None):
         return tc_census64(self.handle, stream)
+
+    def census_matrix(self, stream=None):
+        return tc_census_matrix(self.handle, stream)
 
     def stats(self):
         return tc_graph_stats(self.handle)

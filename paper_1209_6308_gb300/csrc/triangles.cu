@@ -165,6 +165,21 @@ __device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, uint64_t bbas
     return walked;
 }
 
+// A warp's next pairs of the CTA's item: guided sizes, 32 pairs while many remain, then fewer
+// (down to 4) as the item runs out, so that the warps reach the item's end barrier together.
+__device__ __forceinline__ void grab_pairs(uint32_t* s_next, uint32_t j1, int lane, uint32_t& jb, uint32_t& g) {
+    jb = 0;
+    g = 32;
+    if (lane == 0) {
+        const uint32_t cur = *(volatile uint32_t*)s_next;
+        const uint32_t rem = cur < j1 ? j1 - cur : 0u;
+        g = max(4u, min(32u, rem / (2u * kWarps)));
+        jb = atomicAdd(s_next, g);
+    }
+    jb = __shfl_sync(0xffffffffu, jb, 0);
+    g = __shfl_sync(0xffffffffu, g, 0);
+}
+
 // Add a warp's 64 bins to the graph's histogram and clear them (one warp).
 __device__ __forceinline__ void flush_warp_hist(uint32_t* myHist, unsigned long long* hist, int lane) {
     __syncwarp();
@@ -225,11 +240,10 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
             }
             __syncthreads();
             for (;;) {
-                uint32_t jb = 0;
-                if (lane == 0) jb = atomicAdd(&s_next, 32u);
-                jb = __shfl_sync(0xffffffffu, jb, 0);
+                uint32_t jb, g;
+                grab_pairs(&s_next, w.j1, lane, jb, g);
                 if (jb >= w.j1) break;
-                since_flush += walk_pairs<OLD, true>(P, bbase, pb, jb, min(jb + 32u, w.j1), sH, nullptr, 0, 0u, ob,
+                since_flush += walk_pairs<OLD, true>(P, bbase, pb, jb, min(jb + g, w.j1), sH, nullptr, 0, 0u, ob,
                                                      sPerm, myHist, lane);
                 if (since_flush >= kFlushElems) {
                     flush_warp_hist(myHist, P.hist, lane);
@@ -255,11 +269,10 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
             }
             __syncthreads();
             for (;;) {
-                uint32_t jb = 0;
-                if (lane == 0) jb = atomicAdd(&s_next, 32u);
-                jb = __shfl_sync(0xffffffffu, jb, 0);
+                uint32_t jb, g;
+                grab_pairs(&s_next, w.j1, lane, jb, g);
                 if (jb >= w.j1) break;
-                since_flush += walk_pairs<OLD, false>(P, bbase, pb, jb, min(jb + 32u, w.j1), sH, sO, hb, hmask, ob,
+                since_flush += walk_pairs<OLD, false>(P, bbase, pb, jb, min(jb + g, w.j1), sH, sO, hb, hmask, ob,
                                                       sPerm, myHist, lane);
                 if (since_flush >= kFlushElems) {
                     flush_warp_hist(myHist, P.hist, lane);
@@ -309,34 +322,73 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
     flush_warp_hist(myHist, P.hist, lane);
 }
 
-// Bulk counts of the pairs (u, v) with u in [v0, v1), one warp per u, the lanes over its upper
-// pairs: per dir(u,v) code c (tricode bits 1|2, 1..3), raw[7(c-1) + d - 1] += the entries of
-// N[v] past u with direction class d (v-only third vertices before the common ones come
-// off), raw[7(c-1) + 3 + d - 1] += those of N[u] past v (u-only), raw[7(c-1) + 6] += the
-// dyadic base n - d_u - d_v (steps 2.1.2 - 2.1.3 before the common neighbours).
-__global__ void k_pair_bulk(GraphDev g, uint32_t v0, uint32_t v1, unsigned long long* raw) {
+// Bulk counts of the pairs (u, v) with u in [v0, v1): per dir(u,v) code c (tricode bits 1|2,
+// 1..3), raw[7(c-1) + d - 1] += the entries of N[v] past u with direction class d (v-only third
+// vertices before the common ones come off), raw[7(c-1) + 3 + d - 1] += those of N[u] past v
+// (u-only), raw[7(c-1) + 6] += the dyadic base n - d_u - d_v (steps 2.1.2 - 2.1.3 before the
+// common neighbours).  A warp takes 32 consecutive vertices; their upper pairs are consecutive
+// in the table order (ub), so the lanes walk the batch's pairs as one flattened range, reading
+// the tables coalesced, each lane finding its pair's vertex from the vertices' starts.
+__global__ void __launch_bounds__(256, 4) k_pair_bulk(GraphDev g, uint32_t v0, uint32_t v1, unsigned long long* raw) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t le_mask = (2u << lane) - 1u;
     unsigned long long acc[3][7];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int k = 0; k < 7; ++k) acc[c][k] = 0ull;
     const unsigned long long n = g.n;
-    for (uint64_t x = v0 + ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5); x < v1; x += warps) {
-        const uint32_t u = (uint32_t)x;
-        const uint64_t ubase = g.off[u];
-        const uint32_t du = (uint32_t)(g.off[u + 1] - ubase), upu = g.up[u];
-        const uint64_t pb = g.ub[u] - upu;
-        for (uint32_t j = upu + lane; j < du; j += 32) {
-            const uint32_t e = g.adj[ubase + j], v = e >> 2, duv = e & 3u;
+    for (uint64_t base = v0 + 32ull * ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5); base < v1;
+         base += 32ull * warps) {
+        const uint64_t u = base + lane;
+        const bool ok = u < v1;
+        uint64_t ubase = ok ? g.off[u] : 0ull;
+        uint32_t du = ok ? (uint32_t)(g.off[u + 1] - ubase) : 0u;
+        uint32_t upu = ok ? g.up[u] : 0u;
+        uint32_t cnt = du - upu;                  // upper pairs of u (0 past v1)
+        const uint64_t pstart = g.ub[base];       // table index of the batch's first pair
+        // compact the vertices with upper pairs into lanes 0 .. nv-1, keeping their order
+        const uint32_t nz = __ballot_sync(0xffffffffu, cnt != 0u);
+        if (!nz) continue;
+        const uint32_t nv = __popc(nz);
+        const uint32_t src = __fns(nz, 0, lane + 1) & 31u;
+        ubase = __shfl_sync(0xffffffffu, ubase, src);
+        du = __shfl_sync(0xffffffffu, du, src);
+        upu = __shfl_sync(0xffffffffu, upu, src);
+        cnt = __shfl_sync(0xffffffffu, cnt, src);
+        if ((uint32_t)lane >= nv) cnt = 0u;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t excl = incl - cnt;
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        int seg_prev = -1;
+        for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+            const bool st = (uint32_t)lane < nv && excl >= r0 && excl < r0 + 32u;
+            const uint32_t M = __reduce_or_sync(0xffffffffu, st ? (1u << (excl - r0)) : 0u);
+            const int seg = seg_prev + __popc(M & le_mask);
+            seg_prev = __shfl_sync(0xffffffffu, seg, 31);
+            const uint32_t sg = (uint32_t)seg & 31u;
+            const uint32_t sP = __shfl_sync(0xffffffffu, excl, sg);
+            const uint64_t sB = __shfl_sync(0xffffffffu, ubase, sg);
+            const uint32_t sD = __shfl_sync(0xffffffffu, du, sg), sU = __shfl_sync(0xffffffffu, upu, sg);
+            const uint32_t i = r0 + lane;
+            if (i >= total) continue;
+            const uint32_t j = sU + (i - sP);         // the pair's position in N[u]
+            const uint64_t p = pstart + i;            // and in the tables
+            const uint32_t e = g.adj[sB + j], v = e >> 2, duv = e & 3u;
             const uint32_t cuv = ((duv & 1u) << 1) | (duv >> 1);
+            const uint2 vs = g.vs[p], us = g.us[p];
+            const uint32_t rpv = g.rp[p];
             const uint32_t dv = (uint32_t)(g.off[v + 1] - g.off[v]);
-            const uint2 vs = g.vs[pb + j], us = g.us[pb + j];
-            const uint32_t vlen = dv - 1u - g.rp[pb + j], ulen = du - 1u - j;
+            const uint32_t vlen = dv - 1u - rpv, ulen = sD - 1u - j;
             const unsigned long long val[7] = {vs.x, vs.y, (unsigned long long)(vlen - vs.x - vs.y),
                                                us.x, us.y, (unsigned long long)(ulen - us.x - us.y),
-                                               n - du - dv};
+                                               n - sD - dv};
 #pragma unroll
             for (int c = 0; c < 3; ++c)
                 if (cuv == (uint32_t)(c + 1))
@@ -462,7 +514,7 @@ tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* item
     TC_CUDA(cudaMemsetAsync(g.ctr.p, 0, sizeof(uint32_t) * 4, st));
     const GraphDev gd = g.dev();
     if (bulk_v1 > bulk_v0) {
-        k_pair_bulk<<<grid_for((uint64_t)(bulk_v1 - bulk_v0) * 32, 256, 8u * (unsigned)sm_count()), 256, 0, st>>>(
+        k_pair_bulk<<<grid_for((uint64_t)(bulk_v1 - bulk_v0), 256, 4u * (unsigned)sm_count()), 256, 0, st>>>(
             gd, bulk_v0, bulk_v1, raw);
         TC_LAUNCH("k_pair_bulk");
     }
