@@ -63,6 +63,7 @@ def parse(argv=None):
     p.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) run")
     p.add_argument("--no-interval", action="store_true", help="skip the interval (windowed stream) census run")
     p.add_argument("--no-census64", action="store_true", help="skip the 64-state census run")
+    p.add_argument("--no-matrix", action="store_true", help="skip the matrix-form census run")
     p.add_argument("--serve-seconds", type=float, default=60.0, help="measured seconds per serving arm")
     p.add_argument("--serve-warmup", type=float, default=5.0, help="unmeasured seconds before them")
     p.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
@@ -563,6 +564,34 @@ def census64_comparison(tc, torch, sh, scale, steps=3):
             "roofline": roofline_hbm(bytes_alg_8d(n, info), ms, "k_census64")}
 
 
+def matrix_comparison(tc, torch, sh, steps=3):
+    """The matrix form of the census (Sec. 4, tc_census_matrix) on R-MAT scale 14 (ef16, 20%
+    recip, seed 14; n = 2^14, the largest it takes): time per call (CUDA events around the
+    synchronous call: bit matrices, six masked products, 24 sums to the host) and agreement with
+    the triangle form of the Fig. 5 census on the same graph."""
+    import graphgen
+    n, s, d = graphgen.rmat(14, 16, 0.2, 14)
+    from paper_1209_6308_gb300 import learned
+    st = torch.cuda.ExternalStream(sh)
+    with tc.Graph.from_arcs(n, s, d, stream=sh, options={"algo": tc.TC_ALGO_TRIANGLE}) as g:
+        c16 = g.census(stream=sh)
+        cm = g.census_matrix(stream=sh)
+        times = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            cm = g.census_matrix(stream=sh)
+            e1.record(st)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        tri_ms, _ = learned.census_ms(g, {"algo": tc.TC_ALGO_TRIANGLE}, torch.cuda.Stream(), reps=5)
+    ms = statistics.median(times)
+    W = (n + 63) // 64
+    words = 6 * n * n * W       # AND + popcount word operations of the six products
+    return {"workload": "rmat14_ef16_r20_seed14", "n": n, "arcs": len(s), "ms": ms, "equals_census16": cm == c16,
+            "triangle_form_ms": tri_ms, "and_popc_words_per_s": words / (ms * 1e-3)}
+
+
 def roofline_hbm(bytes_alg: int, ms: float, kernel: str, traffic=None, bound="hbm") -> dict:
     peak, peak_kind = measured_peak()
     achieved = bytes_alg / (ms * 1e-3) / 1e9
@@ -747,6 +776,10 @@ def run_gpu(args):
         wl = WORKLOAD if WORKLOAD["scale"] <= 20 else WORKLOADS[20]
         ni, si, di = (n, s, d) if WORKLOAD["scale"] <= 20 else graphgen.rmat(20, 16, 0.2, 2)
         interval_line = interval_comparison(tc, torch, si, di, ni, sh, wl["name"])
+    matrix_line = None
+    if not args.no_matrix:
+        log("matrix census")
+        matrix_line = matrix_comparison(tc, torch, sh)
     census64_lines = None
     if not args.no_census64:
         census64_lines = []
@@ -800,6 +833,8 @@ def run_gpu(args):
         line["interval"] = interval_line
     if census64_lines is not None:
         line["census64"] = census64_lines
+    if matrix_line is not None:
+        line["matrix"] = matrix_line
     if serve_line is not None:
         line["serving"] = serve_line
     if not args.no_batch:

@@ -394,11 +394,8 @@ tc_status tc_census_shard(tc_graph* g, void* stream, const tc_options* opt, uint
     const uint32_t i0 = b[2 * rank], i1 = b[2 * rank + 2];
     const uint32_t v0 = b[2 * rank + 1], v1 = b[2 * rank + 3];
     TC_CUDA(cudaMemsetAsync(d_out16, 0, sizeof(uint64_t) * 16, st));
-    // the triangle form's bulk pair sums: an even slice of the vertices
-    const uint32_t na = g->s.n_active;
-    const uint32_t b0 = (uint32_t)((uint64_t)na * rank / world), b1 = (uint32_t)((uint64_t)na * (rank + 1) / world);
     return census_enqueue_range(g->s, o, p->items.as<Item>() + i0, i1 - i0, p->warp_begin + v0, p->warp_begin + v1, st,
-                                reinterpret_cast<unsigned long long*>(d_out16), nullptr, nullptr, b0, b1);
+                                reinterpret_cast<unsigned long long*>(d_out16));
 }
 
 tc_status tc_census_shard_bounds(tc_graph* g, void* stream, const tc_options* opt, uint32_t world, uint32_t* bounds) {

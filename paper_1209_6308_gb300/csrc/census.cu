@@ -1227,12 +1227,10 @@ tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream
 
 tc_status census_enqueue_range(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
                                uint32_t warp_end, cudaStream_t st, unsigned long long* d_out16,
-                               unsigned long long* d_vcost, unsigned long long* d_phase, uint32_t bulk_v0,
-                               uint32_t bulk_v1) {
+                               unsigned long long* d_vcost, unsigned long long* d_phase) {
     if (g.e_sym == 0) return TC_OK;
     if (o.algo == TC_ALGO_TRIANGLE)
-        return triangle_census_enqueue(g, o, items, n_items, warp_begin, warp_end, bulk_v0,
-                                       bulk_v1 > g.n_active ? g.n_active : bulk_v1, st, d_out16, d_vcost);
+        return triangle_census_enqueue(g, o, items, n_items, warp_begin, warp_end, st, d_out16, d_vcost);
     const bool vt = g.vs.p != nullptr;
     const bool map = census_map(g, o);
     const size_t smem = census_smem(o.algo, o.chunk, map);

@@ -127,17 +127,14 @@ tc_status census_enqueue(GraphStore& g, const Opts& o, const Plan& p, cudaStream
                          unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr);
 // The same census over a part of a plan: items[0, n_items) and warp-tier vertices
 // [warp_begin, warp_end) (a shard; census_enqueue runs the whole plan).
-// The triangle form's bulk pair sums run for the vertices [bulk_v0, bulk_v1) (whole graph by
-// default; a shard takes its own slice).
 tc_status census_enqueue_range(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
                                uint32_t warp_end, cudaStream_t st, unsigned long long* d_out16,
-                               unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr,
-                               uint32_t bulk_v0 = 0, uint32_t bulk_v1 = 0xffffffffu);
-// TC_ALGO_TRIANGLE (triangles.cu): bulk pair sums for [bulk_v0, bulk_v1), the triangle tricode
-// histogram over the given items and warp-tier range, and the fold into d_out16[1..15].
+                               unsigned long long* d_vcost = nullptr, unsigned long long* d_phase = nullptr);
+// TC_ALGO_TRIANGLE (triangles.cu): the bulk pair sums and the triangle tricode histogram over
+// the given items and warp-tier range, and the fold into d_out16[1..15].
 tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items,
-                                  uint32_t warp_begin, uint32_t warp_end, uint32_t bulk_v0, uint32_t bulk_v1,
-                                  cudaStream_t st, unsigned long long* d_out16, unsigned long long* d_vcost);
+                                  uint32_t warp_begin, uint32_t warp_end, cudaStream_t st, unsigned long long* d_out16,
+                                  unsigned long long* d_vcost);
 // The triangle walk alone: histogram of the 64 tricodes (old == nullptr) or of the 64 states in
 // the caller's id order (old = original id per vertex, d_perm_state = [9][64] state of a
 // tricode per rank pattern) of every triangle, added into d_hist64; ctr: 4 zeroed uint32.

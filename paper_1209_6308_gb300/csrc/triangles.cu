@@ -322,16 +322,36 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
     flush_warp_hist(myHist, P.hist, lane);
 }
 
-// Bulk counts of the pairs (u, v) with u in [v0, v1): per dir(u,v) code c (tricode bits 1|2,
-// 1..3), raw[7(c-1) + d - 1] += the entries of N[v] past u with direction class d (v-only third
+// One pair's bulk sums into acc (see k_pair_bulk): u of degree du, the pair's entry e = N[u][j]
+// and its table index p.
+__device__ __forceinline__ void bulk_pair(const GraphDev& g, unsigned long long n, uint32_t du, uint32_t j, uint32_t e,
+                                          uint64_t p, unsigned long long (&acc)[3][7]) {
+    const uint32_t v = e >> 2, duv = e & 3u;
+    const uint32_t cuv = ((duv & 1u) << 1) | (duv >> 1);
+    const uint2 vs = g.vs[p], us = g.us[p];
+    const uint32_t rpv = g.rp[p];
+    const uint32_t dv = (uint32_t)(g.off[v + 1] - g.off[v]);
+    const uint32_t vlen = dv - 1u - rpv, ulen = du - 1u - j;
+    const unsigned long long val[7] = {vs.x, vs.y, (unsigned long long)(vlen - vs.x - vs.y),
+                                       us.x, us.y, (unsigned long long)(ulen - us.x - us.y), n - du - dv};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        if (cuv == (uint32_t)(c + 1))
+#pragma unroll
+            for (int k = 0; k < 7; ++k) acc[c][k] += val[k];
+}
+
+// Bulk counts of the census's pairs: per dir(u,v) code c (tricode bits 1|2, 1..3),
+// raw[7(c-1) + d - 1] += the entries of N[v] past u with direction class d (v-only third
 // vertices before the common ones come off), raw[7(c-1) + 3 + d - 1] += those of N[u] past v
 // (u-only), raw[7(c-1) + 6] += the dyadic base n - d_u - d_v (steps 2.1.2 - 2.1.3 before the
-// common neighbours).  A warp takes 32 consecutive vertices; their upper pairs are consecutive
-// in the table order (ub), so the lanes walk the batch's pairs as one flattened range, reading
-// the tables coalesced, each lane finding its pair's vertex from the vertices' starts.
-__global__ void __launch_bounds__(256, 4) k_pair_bulk(GraphDev g, uint32_t v0, uint32_t v1, unsigned long long* raw) {
+// common neighbours).  The pairs are the plan's: its CTA items (at most kMaxItemPairs pairs of
+// one vertex each, a warp per item), then the one-warp vertices in blocks of 32 consecutive
+// ones, whose upper pairs are consecutive in the table order and are walked as one flattened
+// range.  Work comes from the counters ctr[2] (items) and ctr[3] (blocks), zeroed by the caller.
+__global__ void __launch_bounds__(256, 4) k_pair_bulk(GraphDev g, const Item* __restrict__ items, uint32_t n_items,
+                                                      uint32_t wb, uint32_t we, uint32_t* ctr, unsigned long long* raw) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t le_mask = (2u << lane) - 1u;
     unsigned long long acc[3][7];
 #pragma unroll
@@ -339,15 +359,32 @@ __global__ void __launch_bounds__(256, 4) k_pair_bulk(GraphDev g, uint32_t v0, u
 #pragma unroll
         for (int k = 0; k < 7; ++k) acc[c][k] = 0ull;
     const unsigned long long n = g.n;
-    for (uint64_t base = v0 + 32ull * ((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5); base < v1;
-         base += 32ull * warps) {
+    // the CTA items, a warp each
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(&ctr[2], 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const Item w = items[it];
+        const uint64_t ubase = g.off[w.u];
+        const uint32_t du = (uint32_t)(g.off[w.u + 1] - ubase);
+        const uint64_t pb = g.ub[w.u] - g.up[w.u];
+        for (uint32_t j = w.j0 + lane; j < w.j1; j += 32) bulk_pair(g, n, du, j, g.adj[ubase + j], pb + j, acc);
+    }
+    // the one-warp vertices, 32 consecutive ones per grab
+    for (;;) {
+        uint32_t blk = 0;
+        if (lane == 0) blk = atomicAdd(&ctr[3], 1u);
+        blk = __shfl_sync(0xffffffffu, blk, 0);
+        const uint64_t base = (uint64_t)wb + 32ull * blk;
+        if (base >= we) break;
         const uint64_t u = base + lane;
-        const bool ok = u < v1;
+        const bool ok = u < we;
         uint64_t ubase = ok ? g.off[u] : 0ull;
         uint32_t du = ok ? (uint32_t)(g.off[u + 1] - ubase) : 0u;
         uint32_t upu = ok ? g.up[u] : 0u;
-        uint32_t cnt = du - upu;                  // upper pairs of u (0 past v1)
-        const uint64_t pstart = g.ub[base];       // table index of the batch's first pair
+        uint32_t cnt = du - upu;                  // upper pairs of u (0 past we)
+        const uint64_t pstart = g.ub[base];       // table index of the block's first pair
         // compact the vertices with upper pairs into lanes 0 .. nv-1, keeping their order
         const uint32_t nz = __ballot_sync(0xffffffffu, cnt != 0u);
         if (!nz) continue;
@@ -379,21 +416,7 @@ __global__ void __launch_bounds__(256, 4) k_pair_bulk(GraphDev g, uint32_t v0, u
             const uint32_t i = r0 + lane;
             if (i >= total) continue;
             const uint32_t j = sU + (i - sP);         // the pair's position in N[u]
-            const uint64_t p = pstart + i;            // and in the tables
-            const uint32_t e = g.adj[sB + j], v = e >> 2, duv = e & 3u;
-            const uint32_t cuv = ((duv & 1u) << 1) | (duv >> 1);
-            const uint2 vs = g.vs[p], us = g.us[p];
-            const uint32_t rpv = g.rp[p];
-            const uint32_t dv = (uint32_t)(g.off[v + 1] - g.off[v]);
-            const uint32_t vlen = dv - 1u - rpv, ulen = sD - 1u - j;
-            const unsigned long long val[7] = {vs.x, vs.y, (unsigned long long)(vlen - vs.x - vs.y),
-                                               us.x, us.y, (unsigned long long)(ulen - us.x - us.y),
-                                               n - sD - dv};
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                if (cuv == (uint32_t)(c + 1))
-#pragma unroll
-                    for (int k = 0; k < 7; ++k) acc[c][k] += val[k];
+            bulk_pair(g, n, sD, j, g.adj[sB + j], pstart + i, acc);
         }
     }
 #pragma unroll
@@ -503,8 +526,8 @@ tc_status triangles_launch(const GraphDev& gd, const Opts& o, const Item* items,
 }
 
 tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items,
-                                  uint32_t warp_begin, uint32_t warp_end, uint32_t bulk_v0, uint32_t bulk_v1,
-                                  cudaStream_t st, unsigned long long* d_out16, unsigned long long* d_vcost) {
+                                  uint32_t warp_begin, uint32_t warp_end, cudaStream_t st, unsigned long long* d_out16,
+                                  unsigned long long* d_vcost) {
     if (g.e_sym == 0) return TC_OK;
     if (!g.vs.p) return fail(TC_ERR_ARG, "the triangle form needs the per upper pair tables");
     if (!g.tri.p) TC_TRY(g.tri.alloc_persistent(sizeof(unsigned long long) * 96));
@@ -513,9 +536,10 @@ tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* item
     TC_CUDA(cudaMemsetAsync(raw, 0, sizeof(unsigned long long) * 96, st));
     TC_CUDA(cudaMemsetAsync(g.ctr.p, 0, sizeof(uint32_t) * 4, st));
     const GraphDev gd = g.dev();
-    if (bulk_v1 > bulk_v0) {
-        k_pair_bulk<<<grid_for((uint64_t)(bulk_v1 - bulk_v0), 256, 4u * (unsigned)sm_count()), 256, 0, st>>>(
-            gd, bulk_v0, bulk_v1, raw);
+    const uint64_t units = (uint64_t)n_items + (warp_end - warp_begin + 31u) / 32u;
+    if (units) {
+        k_pair_bulk<<<grid_for(units * 32, 256, 4u * (unsigned)sm_count()), 256, 0, st>>>(
+            gd, items, n_items, warp_begin, warp_end, g.ctr.as<uint32_t>(), raw);
         TC_LAUNCH("k_pair_bulk");
     }
     TC_TRY(triangles_launch(gd, o, items, n_items, warp_begin, warp_end, g.ctr.as<uint32_t>(), nullptr, nullptr, hist,
