@@ -61,7 +61,7 @@ typedef enum {
      * (a < b < c met once, walking the lower-id neighbours of c against those of b), whose
      * tricode fixes the triad and its corrections to the three pairs' bulk and dyadic
      * counts (steps 2.1.2 - 2.1.4).  Needs the per upper pair tables every built graph has;
-     * warp_max_deg <= 128.  Not offered by the batched launch or the server. */
+     * warp_max_deg <= 128.  Not offered by the server. */
     TC_ALGO_TRIANGLE = 2
 } tc_algo;
 
@@ -225,8 +225,8 @@ tc_status tc_batch_census_async(tc_batch* b, void* stream, uint64_t* d_out16xk);
 tc_status tc_batch_census(tc_batch* b, void* stream, uint64_t* out16xk, tc_u128* out003_k);
 
 /* Autotuner: time the batch under candidate kernel forms and tile and tier thresholds by
- * coordinate descent from the batch's current options - algo {union, suffix}, warp_max_deg
- * {16..256}, chunk_entries {1024..8192}, ctas_per_sm {2, 3, 4}, item_work {sized to the
+ * coordinate descent from the batch's current options - algo {union, suffix, triangle},
+ * warp_max_deg {16..256}, chunk_entries {1024..8192}, ctas_per_sm {2..8}, item_work {sized to the
  * graphs, 2^14..2^22} - one at a time, keeping the best value of each, for up to three passes
  * or until a pass gains under 1% (at most max_trials timed plans, 0 = no limit; each timed as
  * the median of three replays after one untimed one).  Keeps the fastest plan in the batch and

@@ -105,6 +105,7 @@ struct BatchStore {
     Opts opts;
     cudaStream_t cap = nullptr;         // stream used only to capture the launch
     DevBuf d_graphs, d_voff, d_woff, d_wide, d_order, items, wblocks, ctr, out;
+    DevBuf tri;                         // triangle form: 96 uint64 of scratch per graph
     uint32_t n_items = 0, n_wblocks = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -196,13 +197,21 @@ tc_status batch_plan(BatchStore& b, cudaStream_t st) {
         TC_CUDA(cudaMemcpyAsync(b.wblocks.p, wb.data(), sizeof(uint4) * wb.size(), cudaMemcpyHostToDevice, st));
     TC_CUDA(cudaStreamSynchronize(st));
     // capture: zero counters and outputs, launch
-    TC_TRY(census_prepare(st, o));
+    if (o.algo == TC_ALGO_TRIANGLE) {
+        if (!b.tri.p) TC_TRY(b.tri.alloc_persistent(sizeof(unsigned long long) * 96ull * (k ? k : 1)));
+    } else {
+        TC_TRY(census_prepare(st, o));
+    }
     TC_CUDA(cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeThreadLocal));
     tc_status s = TC_OK;
     if (cudaMemsetAsync(b.ctr.p, 0, sizeof(uint32_t) * 4, b.cap) != cudaSuccess ||
         cudaMemsetAsync(b.out.p, 0, sizeof(unsigned long long) * 16ull * k, b.cap) != cudaSuccess)
         s = fail(TC_ERR_CUDA, "batch capture: memset failed");
-    if (s == TC_OK)
+    if (s == TC_OK && o.algo == TC_ALGO_TRIANGLE)
+        s = triangle_census_batch(b.d_graphs.as<GraphDev>(), k, b.items.as<Item>(), b.n_items, b.wblocks.as<uint4>(),
+                                  b.n_wblocks, o, b.ctr.as<uint32_t>(), b.tri.as<unsigned long long>(),
+                                  b.out.as<unsigned long long>(), b.cap);
+    else if (s == TC_OK)
         s = census_launch_batch(b.d_graphs.as<GraphDev>(), b.items.as<Item>(), b.n_items, b.wblocks.as<uint4>(),
                                 b.n_wblocks, o, b.ctr.as<uint32_t>(), b.out.as<unsigned long long>(), b.cap);
     cudaGraph_t gph = nullptr;
@@ -242,8 +251,6 @@ tc_status tc_batch_create(tc_graph* const* gs, uint32_t k, const tc_options* opt
     BatchStore& B = b->s;
     B.k = k;
     tc_status s = resolve_opts(opt, nullptr, &B.opts);
-    if (s == TC_OK && B.opts.algo == TC_ALGO_TRIANGLE)
-        s = fail(TC_ERR_ARG, "the batched launch runs the union or suffix form");
     for (uint32_t i = 0; s == TC_OK && i < k; ++i)
         if (!gs[i]) s = fail(TC_ERR_ARG, "null graph in batch");
     if (s == TC_OK) {
@@ -328,6 +335,7 @@ tc_options to_options(const Opts& o) {
 
 bool valid_batch_opts(const Opts& o) {
     const uint32_t max_chunk = o.algo == TC_ALGO_UNION ? 16384u : 8192u;
+    if (o.algo == TC_ALGO_TRIANGLE && o.warp_max_deg > 128) return false;
     return o.chunk >= 512 && o.chunk <= max_chunk && o.warp_max_deg <= o.chunk / 8 && o.ctas_per_sm >= 1 &&
            o.ctas_per_sm <= 8;
 }
@@ -377,10 +385,10 @@ tc_status tc_batch_autotune(tc_batch* b, void* stream, uint32_t max_trials, tc_o
         const float pass_start = best;
         for (int dim = 0; dim < 5 && s == TC_OK; ++dim) {
             std::vector<uint32_t> vals;
-            if (dim == 0) vals = {TC_ALGO_UNION, TC_ALGO_SUFFIX};
+            if (dim == 0) vals = {TC_ALGO_UNION, TC_ALGO_SUFFIX, TC_ALGO_TRIANGLE};
             if (dim == 1) vals = {16u, 32u, 64u, 128u, 256u};
             if (dim == 2) vals = {1024u, 2048u, 4096u, 8192u};
-            if (dim == 3) vals = {2u, 3u, 4u};
+            if (dim == 3) vals = {2u, 3u, 4u, 6u, 8u};
             if (dim == 4) vals = {0u, 1u << 14, 1u << 16, 1u << 18, 1u << 20, 1u << 22};
             for (uint32_t v : vals) {
                 if (max_trials && trials >= max_trials) break;

@@ -135,6 +135,12 @@ tc_status census_enqueue_range(GraphStore& g, const Opts& o, const Item* items, 
 tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items,
                                   uint32_t warp_begin, uint32_t warp_end, cudaStream_t st, unsigned long long* d_out16,
                                   unsigned long long* d_vcost);
+// Batched triangle form: k graphs (d_graphs), items tagged with the graph (pad), warp-tier
+// blocks (u0, u1, graph); d_scratch holds 96 uint64 per graph (zeroed here), graph g's counts of
+// classes 1..15 are added to d_out[16 g ..] (caller-zeroed); ctr: 4 zeroed uint32.
+tc_status triangle_census_batch(const GraphDev* d_graphs, uint32_t k, const Item* items, uint32_t n_items,
+                                const uint4* wblocks, uint32_t n_wblocks, const Opts& o, uint32_t* ctr,
+                                unsigned long long* d_scratch, unsigned long long* d_out, cudaStream_t st);
 // The triangle walk alone: histogram of the 64 tricodes (old == nullptr) or of the 64 states in
 // the caller's id order (old = original id per vertex, d_perm_state = [9][64] state of a
 // tricode per rank pattern) of every triangle, added into d_hist64; ctr: 4 zeroed uint32.

@@ -60,9 +60,18 @@ struct TriParams {
     uint32_t* ctr;                // [0] next item, [1] next warp-tier vertex
     const uint32_t* old;          // OLD: the caller's id of each vertex
     const uint8_t* perm_state;    // OLD: [9][64] state of a tricode under the rank pattern 3 ra + rb
-    unsigned long long* hist;     // 64 bins (triangle tricodes, or states with OLD)
+    unsigned long long* hist;     // 64 bins (triangle tricodes, or states with OLD); batched: graph g's at
+                                  // hist + kBatchStride g
     unsigned long long* vcost;    // optional [n]: SM cycles per CTA-tier vertex b
+    // batched launch: item.pad is the graph index, warp-tier blocks are (u0, u1, graph)
+    const GraphDev* graphs;
+    const uint4* wblocks;
+    uint32_t n_wblocks;
 };
+
+// batched triangle form: per graph 96 uint64 of scratch, the 21 bulk sums at [0, 21) and the 64
+// triangle tricodes at [32, 96)
+constexpr uint32_t kBatchStride = 96;
 
 // Walk, for the pairs (b, c = N[b][j]), j in [j0, j1), 32 pairs per batch, the entries of N[c]
 // below b (rp = b's position in N[c], from the pair tables; pb + j indexes the pair) and count
@@ -70,13 +79,13 @@ struct TriParams {
 // a < b is in its range); else a hash.  One warp; the lanes share each batch's flattened (pair,
 // position) range.  Returns the entries walked (warp-uniform).
 template <bool OLD, bool MAP>
-__device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, uint64_t bbase, uint64_t pb, uint32_t j0,
-                                               uint32_t j1, const uint32_t* sH, const uint32_t* sO, int hb,
-                                               uint32_t hmask, uint32_t ob, const uint8_t* sPerm, uint32_t* myHist,
-                                               int lane) {
-    const uint64_t* __restrict__ off = P.g.off;
-    const uint32_t* __restrict__ adj = P.g.adj;
-    const uint32_t* __restrict__ rp = P.g.rp;
+__device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, const GraphDev& G, uint64_t bbase, uint64_t pb,
+                                               uint32_t j0, uint32_t j1, const uint32_t* sH, const uint32_t* sO,
+                                               int hb, uint32_t hmask, uint32_t ob, const uint8_t* sPerm,
+                                               uint32_t* myHist, int lane) {
+    const uint64_t* __restrict__ off = G.off;
+    const uint32_t* __restrict__ adj = G.adj;
+    const uint32_t* __restrict__ rp = G.rp;
     const uint32_t le_mask = (2u << lane) - 1u;
     uint32_t walked = 0;
     for (uint32_t jb = j0; jb < j1; jb += 32) {
@@ -191,7 +200,7 @@ __device__ __forceinline__ void flush_warp_hist(uint32_t* myHist, unsigned long 
     __syncwarp();
 }
 
-template <bool OLD>
+template <bool OLD, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t slots = 2u * P.chunk;
@@ -209,9 +218,16 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
         for (int k = tid; k < 9 * 64; k += kThreads) sPerm[k] = P.perm_state[k];
     __syncthreads();
     uint32_t* myHist = sHist + warp * 64;
-    const uint64_t* __restrict__ off = P.g.off;
-    const uint32_t* __restrict__ adj = P.g.adj;
-    const uint32_t* __restrict__ up = P.g.up;
+    GraphDev G = P.g;
+    unsigned long long* ghist = P.hist;
+    uint32_t cur_graph = 0xffffffffu;   // batched: the graph whose counts the warp's bins hold
+    // batched: move to graph gi, flushing this warp's bins to the graph they belong to
+    auto use_graph = [&](uint32_t gi) {
+        if (cur_graph != 0xffffffffu) flush_warp_hist(myHist, ghist, lane);
+        cur_graph = gi;
+        G = P.graphs[gi];
+        ghist = P.hist + (uint64_t)kBatchStride * gi;
+    };
     uint32_t since_flush = 0;   // warp-uniform: entries walked since this warp's bins were flushed
     // the hash region (2 x chunk words) holds a direct map of 32 x chunk ids at two bits each
     const uint32_t map_ids = 32u * P.chunk;
@@ -223,19 +239,20 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
         const uint32_t it = s_item;
         if (it >= P.n_items) break;
         const Item w = P.items[it];
+        if (BATCH && w.pad != cur_graph) use_graph(w.pad);
         const long long t0 = clock64();
         const uint32_t b = w.u;
-        const uint64_t bbase = off[b];
-        const uint32_t lb = up[b];
+        const uint64_t bbase = G.off[b];
+        const uint32_t lb = G.up[b];
         const uint32_t ob = OLD ? P.old[b] : 0u;
-        const uint64_t pb = P.g.ub[b] - lb;   // table index of the pair (b, N[b][j]) is pb + j
+        const uint64_t pb = G.ub[b] - lb;   // table index of the pair (b, N[b][j]) is pb + j
         if (b <= map_ids) {
             // L(b) as a direct map of two direction bits per id below b: one pass, no probing
             for (uint32_t k = tid; k < map_ids / 16u; k += kThreads) sH[k] = 0u;
             if (tid == 0) s_next = w.j0;
             __syncthreads();
             for (uint32_t k = tid; k < lb; k += kThreads) {
-                const uint32_t e = adj[bbase + k], a = e >> 2;
+                const uint32_t e = G.adj[bbase + k], a = e >> 2;
                 atomicOr(&sH[a >> 4], (e & 3u) << ((a & 15u) << 1));
             }
             __syncthreads();
@@ -243,10 +260,10 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
                 uint32_t jb, g;
                 grab_pairs(&s_next, w.j1, lane, jb, g);
                 if (jb >= w.j1) break;
-                since_flush += walk_pairs<OLD, true>(P, bbase, pb, jb, min(jb + g, w.j1), sH, nullptr, 0, 0u, ob,
+                since_flush += walk_pairs<OLD, true>(P, G, bbase, pb, jb, min(jb + g, w.j1), sH, nullptr, 0, 0u, ob,
                                                      sPerm, myHist, lane);
                 if (since_flush >= kFlushElems) {
-                    flush_warp_hist(myHist, P.hist, lane);
+                    flush_warp_hist(myHist, ghist, lane);
                     since_flush = 0;
                 }
             }
@@ -262,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
             if (tid == 0) s_next = w.j0;
             __syncthreads();
             for (uint32_t k = tid; k < LA; k += kThreads) {
-                const uint32_t e = adj[bbase + c0 + k];
+                const uint32_t e = G.adj[bbase + c0 + k];
                 uint32_t h = tri_hash(e >> 2, hb);
                 while (atomicCAS(&sH[h], 0u, e) != 0u) h = (h + 1u) & hmask;
                 if (OLD) sO[h] = P.old[e >> 2];
@@ -272,10 +289,10 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
                 uint32_t jb, g;
                 grab_pairs(&s_next, w.j1, lane, jb, g);
                 if (jb >= w.j1) break;
-                since_flush += walk_pairs<OLD, false>(P, bbase, pb, jb, min(jb + g, w.j1), sH, sO, hb, hmask, ob,
+                since_flush += walk_pairs<OLD, false>(P, G, bbase, pb, jb, min(jb + g, w.j1), sH, sO, hb, hmask, ob,
                                                       sPerm, myHist, lane);
                 if (since_flush >= kFlushElems) {
-                    flush_warp_hist(myHist, P.hist, lane);
+                    flush_warp_hist(myHist, ghist, lane);
                     since_flush = 0;
                 }
             }
@@ -289,14 +306,27 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
     uint32_t* wH = sWH + warp * kWarpSlots;
     uint32_t* wO = sWO + (OLD ? warp * kWarpSlots : 0u);
     for (;;) {
-        uint32_t vb = 0;
-        if (lane == 0) vb = atomicAdd(&P.ctr[1], 1u << P.wshift);
-        vb = __shfl_sync(0xffffffffu, vb, 0);
-        if (vb >= P.warp_end - P.warp_begin) break;
-        const uint32_t b0 = P.warp_begin + vb, b1 = min(b0 + (1u << P.wshift), P.warp_end);
+        uint32_t b0, b1;
+        if (BATCH) {
+            uint32_t bk = 0;
+            if (lane == 0) bk = atomicAdd(&P.ctr[1], 1u);
+            bk = __shfl_sync(0xffffffffu, bk, 0);
+            if (bk >= P.n_wblocks) break;
+            const uint4 wb = P.wblocks[bk];
+            if (wb.z != cur_graph) use_graph(wb.z);
+            b0 = wb.x;
+            b1 = wb.y;
+        } else {
+            uint32_t vb = 0;
+            if (lane == 0) vb = atomicAdd(&P.ctr[1], 1u << P.wshift);
+            vb = __shfl_sync(0xffffffffu, vb, 0);
+            if (vb >= P.warp_end - P.warp_begin) break;
+            b0 = P.warp_begin + vb;
+            b1 = min(b0 + (1u << P.wshift), P.warp_end);
+        }
         for (uint32_t b = b0; b < b1; ++b) {
-            const uint64_t bbase = off[b];
-            const uint32_t db = (uint32_t)(off[b + 1] - bbase), lb = up[b];
+            const uint64_t bbase = G.off[b];
+            const uint32_t db = (uint32_t)(G.off[b + 1] - bbase), lb = G.up[b];
             if (lb == 0u || lb >= db) continue;   // no lower or no upper neighbour: no triangle has b in the middle
             int hb = 6;
             while ((1u << hb) < 2u * lb) ++hb;
@@ -305,21 +335,21 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
             for (uint32_t k = lane; k < (1u << hb); k += 32) wH[k] = 0u;
             __syncwarp();
             for (uint32_t k = lane; k < lb; k += 32) {
-                const uint32_t e = adj[bbase + k];
+                const uint32_t e = G.adj[bbase + k];
                 uint32_t h = tri_hash(e >> 2, hb);
                 while (atomicCAS(&wH[h], 0u, e) != 0u) h = (h + 1u) & hmask;
                 if (OLD) wO[h] = P.old[e >> 2];
             }
             __syncwarp();
-            since_flush += walk_pairs<OLD, false>(P, bbase, P.g.ub[b] - lb, lb, db, wH, wO, hb, hmask,
+            since_flush += walk_pairs<OLD, false>(P, G, bbase, G.ub[b] - lb, lb, db, wH, wO, hb, hmask,
                                                   OLD ? P.old[b] : 0u, sPerm, myHist, lane);
             if (since_flush >= kFlushElems) {
-                flush_warp_hist(myHist, P.hist, lane);
+                flush_warp_hist(myHist, ghist, lane);
                 since_flush = 0;
             }
         }
     }
-    flush_warp_hist(myHist, P.hist, lane);
+    if (!BATCH || cur_graph != 0xffffffffu) flush_warp_hist(myHist, ghist, lane);
 }
 
 // One pair's bulk sums into acc (see k_pair_bulk): u of degree du, the pair's entry e = N[u][j]
@@ -349,8 +379,33 @@ __device__ __forceinline__ void bulk_pair(const GraphDev& g, unsigned long long 
 // one vertex each, a warp per item), then the one-warp vertices in blocks of 32 consecutive
 // ones, whose upper pairs are consecutive in the table order and are walked as one flattened
 // range.  Work comes from the counters ctr[2] (items) and ctr[3] (blocks), zeroed by the caller.
-__global__ void __launch_bounds__(256, 4) k_pair_bulk(GraphDev g, const Item* __restrict__ items, uint32_t n_items,
-                                                      uint32_t wb, uint32_t we, uint32_t* ctr, unsigned long long* raw) {
+// BATCH: item.pad and the blocks' third field name the graph (graphs[g], sums at raw + kBatchStride g).
+struct BulkParams {
+    GraphDev g;
+    const Item* items;
+    uint32_t n_items;
+    uint32_t wb, we;              // single graph: the one-warp vertices
+    const GraphDev* graphs;       // batched
+    const uint4* wblocks;
+    uint32_t n_wblocks;
+    uint32_t* ctr;
+    unsigned long long* raw;
+};
+
+__device__ __forceinline__ void flush_bulk(unsigned long long (&acc)[3][7], unsigned long long* raw, uint32_t lane) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            unsigned long long s = acc[c][k];
+            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0 && s) atomicAdd(&raw[7 * c + k], s);
+            acc[c][k] = 0ull;
+        }
+}
+
+template <bool BATCH>
+__global__ void __launch_bounds__(256, 4) k_pair_bulk(BulkParams P) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t le_mask = (2u << lane) - 1u;
     unsigned long long acc[3][7];
@@ -358,33 +413,54 @@ __global__ void __launch_bounds__(256, 4) k_pair_bulk(GraphDev g, const Item* __
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int k = 0; k < 7; ++k) acc[c][k] = 0ull;
-    const unsigned long long n = g.n;
+    GraphDev G = P.g;
+    unsigned long long* raw = P.raw;
+    uint32_t cur_graph = 0xffffffffu;
+    auto use_graph = [&](uint32_t gi) {
+        if (cur_graph != 0xffffffffu) flush_bulk(acc, raw, lane);
+        cur_graph = gi;
+        G = P.graphs[gi];
+        raw = P.raw + (uint64_t)kBatchStride * gi;
+    };
     // the CTA items, a warp each
     for (;;) {
         uint32_t it = 0;
-        if (lane == 0) it = atomicAdd(&ctr[2], 1u);
+        if (lane == 0) it = atomicAdd(&P.ctr[2], 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= n_items) break;
-        const Item w = items[it];
-        const uint64_t ubase = g.off[w.u];
-        const uint32_t du = (uint32_t)(g.off[w.u + 1] - ubase);
-        const uint64_t pb = g.ub[w.u] - g.up[w.u];
-        for (uint32_t j = w.j0 + lane; j < w.j1; j += 32) bulk_pair(g, n, du, j, g.adj[ubase + j], pb + j, acc);
+        if (it >= P.n_items) break;
+        const Item w = P.items[it];
+        if (BATCH && w.pad != cur_graph) use_graph(w.pad);
+        const unsigned long long n = G.n;
+        const uint64_t ubase = G.off[w.u];
+        const uint32_t du = (uint32_t)(G.off[w.u + 1] - ubase);
+        const uint64_t pb = G.ub[w.u] - G.up[w.u];
+        for (uint32_t j = w.j0 + lane; j < w.j1; j += 32) bulk_pair(G, n, du, j, G.adj[ubase + j], pb + j, acc);
     }
     // the one-warp vertices, 32 consecutive ones per grab
     for (;;) {
         uint32_t blk = 0;
-        if (lane == 0) blk = atomicAdd(&ctr[3], 1u);
+        if (lane == 0) blk = atomicAdd(&P.ctr[3], 1u);
         blk = __shfl_sync(0xffffffffu, blk, 0);
-        const uint64_t base = (uint64_t)wb + 32ull * blk;
-        if (base >= we) break;
+        uint64_t base, end;
+        if (BATCH) {
+            if (blk >= P.n_wblocks) break;
+            const uint4 wbk = P.wblocks[blk];
+            if (wbk.z != cur_graph) use_graph(wbk.z);
+            base = wbk.x;
+            end = wbk.y;
+        } else {
+            base = (uint64_t)P.wb + 32ull * blk;
+            if (base >= P.we) break;
+            end = base + 32u < P.we ? base + 32u : P.we;
+        }
+        const unsigned long long n = G.n;
         const uint64_t u = base + lane;
-        const bool ok = u < we;
-        uint64_t ubase = ok ? g.off[u] : 0ull;
-        uint32_t du = ok ? (uint32_t)(g.off[u + 1] - ubase) : 0u;
-        uint32_t upu = ok ? g.up[u] : 0u;
-        uint32_t cnt = du - upu;                  // upper pairs of u (0 past we)
-        const uint64_t pstart = g.ub[base];       // table index of the block's first pair
+        const bool ok = u < end;
+        uint64_t ubase = ok ? G.off[u] : 0ull;
+        uint32_t du = ok ? (uint32_t)(G.off[u + 1] - ubase) : 0u;
+        uint32_t upu = ok ? G.up[u] : 0u;
+        uint32_t cnt = du - upu;                  // upper pairs of u (0 past the block)
+        const uint64_t pstart = G.ub[base];       // table index of the block's first pair
         // compact the vertices with upper pairs into lanes 0 .. nv-1, keeping their order
         const uint32_t nz = __ballot_sync(0xffffffffu, cnt != 0u);
         if (!nz) continue;
@@ -416,17 +492,10 @@ __global__ void __launch_bounds__(256, 4) k_pair_bulk(GraphDev g, const Item* __
             const uint32_t i = r0 + lane;
             if (i >= total) continue;
             const uint32_t j = sU + (i - sP);         // the pair's position in N[u]
-            bulk_pair(g, n, sD, j, g.adj[sB + j], pstart + i, acc);
+            bulk_pair(G, n, sD, j, G.adj[sB + j], pstart + i, acc);
         }
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            unsigned long long s = acc[c][k];
-            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0 && s) atomicAdd(&raw[7 * c + k], s);
-        }
+    if (!BATCH || cur_graph != 0xffffffffu) flush_bulk(acc, raw, lane);
 }
 
 struct Table64 {
@@ -435,10 +504,14 @@ struct Table64 {
 
 // 16 classes from the bulk sums and the triangle tricodes (see the file comment); adds
 // classes 1..15 into out16 (index 0 untouched).  One block of 64 threads.
+// Batched: block g folds raw + kBatchStride g and hist + kBatchStride g into out16 + 16 g.
 __global__ void k_tri_fold(const unsigned long long* __restrict__ raw, const unsigned long long* __restrict__ hist,
                            Table64 T, unsigned long long* out16) {
     __shared__ unsigned long long s[16];
     const uint32_t t = threadIdx.x;
+    raw += (uint64_t)kBatchStride * blockIdx.x;
+    hist += (uint64_t)kBatchStride * blockIdx.x;
+    out16 += 16ull * blockIdx.x;
     if (t < 16) s[t] = 0ull;
     __syncthreads();
     if (t < 21) {
@@ -470,7 +543,7 @@ __global__ void k_tri_fold(const unsigned long long* __restrict__ raw, const uns
     if (t >= 1 && t < 16 && s[t]) atomicAdd(&out16[t], s[t]);
 }
 
-std::atomic<uint64_t> g_tri_attr[2] = {};
+std::atomic<uint64_t> g_tri_attr[3] = {};
 
 size_t tri_smem(uint32_t chunk, bool old) {
     const size_t slots = 2ull * chunk;
@@ -478,21 +551,31 @@ size_t tri_smem(uint32_t chunk, bool old) {
            (old ? 9 * 64 : 0);
 }
 
-tc_status tri_prepare(bool old, size_t smem) {
+// form: 0 single graph, 1 caller-id states (64-state census), 2 batched
+tc_status tri_prepare(int form, size_t smem) {
     int dev = 0;
     TC_CUDA(cudaGetDevice(&dev));
     const uint64_t bit = 1ull << (dev & 63);
-    const void* fn = old ? (const void*)k_triangles<true> : (const void*)k_triangles<false>;
+    const void* fns[3] = {(const void*)k_triangles<false, false>, (const void*)k_triangles<true, false>,
+                          (const void*)k_triangles<false, true>};
+    const void* fn = fns[form];
     int optin = 0;
     TC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     cudaFuncAttributes fa;
     TC_CUDA(cudaFuncGetAttributes(&fa, fn));
     const int lim = optin - (int)fa.sharedSizeBytes;
     if ((int)smem > lim) return fail(TC_ERR_ARG, "chunk_entries too large for this GPU's shared memory");
-    if (!(g_tri_attr[old ? 1 : 0].load() & bit)) {
+    if (!(g_tri_attr[form].load() & bit)) {
         TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        g_tri_attr[old ? 1 : 0].fetch_or(bit);
+        g_tri_attr[form].fetch_or(bit);
     }
+    return TC_OK;
+}
+
+tc_status fold_table(Table64* T) {
+    const uint8_t* ht = host_tricode_table();
+    if (!ht) return fail(TC_ERR_ARG, "tricode table derivation failed");
+    std::memcpy(T->t, ht, 64);
     return TC_OK;
 }
 
@@ -503,7 +586,7 @@ tc_status triangles_launch(const GraphDev& gd, const Opts& o, const Item* items,
                            unsigned long long* d_hist64, unsigned long long* d_vcost, cudaStream_t st) {
     const bool is_old = old != nullptr;
     const size_t smem = tri_smem(o.chunk, is_old);
-    TC_TRY(tri_prepare(is_old, smem));
+    TC_TRY(tri_prepare(is_old ? 1 : 0, smem));
     TriParams P;
     std::memset(&P, 0, sizeof(P));
     P.g = gd;
@@ -519,8 +602,8 @@ tc_status triangles_launch(const GraphDev& gd, const Opts& o, const Item* items,
     P.hist = d_hist64;
     P.vcost = d_vcost;
     const unsigned grid = (unsigned)census_grid(o);
-    if (is_old) k_triangles<true><<<grid, kThreads, smem, st>>>(P);
-    else k_triangles<false><<<grid, kThreads, smem, st>>>(P);
+    if (is_old) k_triangles<true, false><<<grid, kThreads, smem, st>>>(P);
+    else k_triangles<false, false><<<grid, kThreads, smem, st>>>(P);
     TC_LAUNCH("k_triangles");
     return TC_OK;
 }
@@ -530,26 +613,72 @@ tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* item
                                   unsigned long long* d_vcost) {
     if (g.e_sym == 0) return TC_OK;
     if (!g.vs.p) return fail(TC_ERR_ARG, "the triangle form needs the per upper pair tables");
-    if (!g.tri.p) TC_TRY(g.tri.alloc_persistent(sizeof(unsigned long long) * 96));
+    if (!g.tri.p) TC_TRY(g.tri.alloc_persistent(sizeof(unsigned long long) * kBatchStride));
     unsigned long long* raw = g.tri.as<unsigned long long>();   // [0, 21) bulk sums, [32, 96) triangle tricodes
     unsigned long long* hist = raw + 32;
-    TC_CUDA(cudaMemsetAsync(raw, 0, sizeof(unsigned long long) * 96, st));
+    TC_CUDA(cudaMemsetAsync(raw, 0, sizeof(unsigned long long) * kBatchStride, st));
     TC_CUDA(cudaMemsetAsync(g.ctr.p, 0, sizeof(uint32_t) * 4, st));
     const GraphDev gd = g.dev();
     const uint64_t units = (uint64_t)n_items + (warp_end - warp_begin + 31u) / 32u;
     if (units) {
-        k_pair_bulk<<<grid_for(units * 32, 256, 4u * (unsigned)sm_count()), 256, 0, st>>>(
-            gd, items, n_items, warp_begin, warp_end, g.ctr.as<uint32_t>(), raw);
+        BulkParams B;
+        std::memset(&B, 0, sizeof(B));
+        B.g = gd;
+        B.items = items;
+        B.n_items = n_items;
+        B.wb = warp_begin;
+        B.we = warp_end;
+        B.ctr = g.ctr.as<uint32_t>();
+        B.raw = raw;
+        k_pair_bulk<false><<<grid_for(units * 32, 256, 4u * (unsigned)sm_count()), 256, 0, st>>>(B);
         TC_LAUNCH("k_pair_bulk");
     }
     TC_TRY(triangles_launch(gd, o, items, n_items, warp_begin, warp_end, g.ctr.as<uint32_t>(), nullptr, nullptr, hist,
                             d_vcost, st));
     Table64 T;
-    const uint8_t* ht = host_tricode_table();
-    if (!ht) return fail(TC_ERR_ARG, "tricode table derivation failed");
-    std::memcpy(T.t, ht, 64);
+    TC_TRY(fold_table(&T));
     k_tri_fold<<<1, 64, 0, st>>>(raw, hist, T, d_out16);
     TC_LAUNCH("k_tri_fold");
+    return TC_OK;
+}
+
+tc_status triangle_census_batch(const GraphDev* d_graphs, uint32_t k, const Item* items, uint32_t n_items,
+                                const uint4* wblocks, uint32_t n_wblocks, const Opts& o, uint32_t* ctr,
+                                unsigned long long* d_scratch, unsigned long long* d_out, cudaStream_t st) {
+    if (k == 0) return TC_OK;
+    const size_t smem = tri_smem(o.chunk, false);
+    TC_TRY(tri_prepare(2, smem));
+    TC_CUDA(cudaMemsetAsync(d_scratch, 0, sizeof(unsigned long long) * kBatchStride * k, st));
+    const uint64_t units = (uint64_t)n_items + n_wblocks;
+    if (units) {
+        BulkParams B;
+        std::memset(&B, 0, sizeof(B));
+        B.items = items;
+        B.n_items = n_items;
+        B.graphs = d_graphs;
+        B.wblocks = wblocks;
+        B.n_wblocks = n_wblocks;
+        B.ctr = ctr;
+        B.raw = d_scratch;
+        k_pair_bulk<true><<<grid_for(units * 32, 256, 4u * (unsigned)sm_count()), 256, 0, st>>>(B);
+        TC_LAUNCH("k_pair_bulk (batched)");
+        TriParams P;
+        std::memset(&P, 0, sizeof(P));
+        P.items = items;
+        P.n_items = n_items;
+        P.chunk = o.chunk;
+        P.ctr = ctr;
+        P.hist = d_scratch + 32;
+        P.graphs = d_graphs;
+        P.wblocks = wblocks;
+        P.n_wblocks = n_wblocks;
+        k_triangles<false, true><<<(unsigned)census_grid(o), kThreads, smem, st>>>(P);
+        TC_LAUNCH("k_triangles (batched)");
+    }
+    Table64 T;
+    TC_TRY(fold_table(&T));
+    k_tri_fold<<<k, 64, 0, st>>>(d_scratch, d_scratch + 32, T, d_out);
+    TC_LAUNCH("k_tri_fold (batched)");
     return TC_OK;
 }
 

@@ -44,6 +44,13 @@ def test_batch_matches_oracle(tc, mixed):
     gs, arcs = mixed
     want = [oracle.census_bm(n, s, d) for (n, s, d) in arcs]
     assert tc.tc_census_batch([g.handle for g in gs]) == want
+    for opts in ({"algo": 2}, {"algo": 2, "ctas_per_sm": 3, "chunk_entries": 1024, "item_work": 2048}):
+        b = tc.tc_batch_create([g.handle for g in gs], options=opts)
+        try:
+            assert tc.tc_batch_census(b, len(gs)) == want, opts
+            assert tc.tc_batch_census(b, len(gs)) == want, opts      # replays start from zero
+        finally:
+            tc.tc_batch_destroy(b)
 
 
 def test_batch_object_replays_and_keeps_caller_order(tc, mixed):
@@ -78,15 +85,15 @@ def test_autotuned_plan_is_exact(tc, mixed):
         hist = tc.tc_batch_autotune_history(b)
         assert len(hist) > 6 and all(t > 0 for _, t in hist)
         assert ms == min(t for _, t in hist) and hist[0][1] >= ms
-        assert {o["algo"] for o, _ in hist} == {0, 1}
-        assert {o["ctas_per_sm"] for o, _ in hist} >= {2, 3, 4}
+        assert {o["algo"] for o, _ in hist} == {0, 1, 2}
+        assert {o["ctas_per_sm"] for o, _ in hist} >= {2, 3, 4, 6, 8}
         assert tc.tc_batch_census(b, len(gs)) == want
     finally:
         tc.tc_batch_destroy(b)
 
 
-@pytest.mark.parametrize("algo", [0, 1])
-def test_batch_union_and_suffix(tc, mixed, algo):
+@pytest.mark.parametrize("algo", [0, 1, 2])
+def test_batch_every_form(tc, mixed, algo):
     gs, arcs = mixed
     want = [g.census() for g in gs]
     b = tc.tc_batch_create([g.handle for g in gs], options={"algo": algo, "warp_max_deg": 8, "chunk_entries": 512})

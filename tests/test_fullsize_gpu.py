@@ -64,13 +64,14 @@ def test_batch_4096_persistent_launch_matches_oracle(tc, batch_graphs):
     got = tc.tc_census_batch([g.handle for g in gs])
     bad = [i for i, (a, b) in enumerate(zip(got, want)) if a != b]
     assert not bad, f"{len(bad)} graphs differ, first {bad[:5]}"
-    b = tc.tc_batch_create([g.handle for g in gs], options={"algo": 1})
-    try:
-        tc.tc_batch_autotune(b, max_trials=8)
-        got = tc.tc_batch_census(b, len(gs))
-        assert got == want
-    finally:
-        tc.tc_batch_destroy(b)
+    for opts in ({"algo": 1}, {"algo": 2}):
+        b = tc.tc_batch_create([g.handle for g in gs], options=opts)
+        try:
+            assert tc.tc_batch_census(b, len(gs)) == want, opts
+            tc.tc_batch_autotune(b, max_trials=8)
+            assert tc.tc_batch_census(b, len(gs)) == want, opts
+        finally:
+            tc.tc_batch_destroy(b)
 
 
 @pytest.mark.parametrize("algo", [0, 1, 2])
