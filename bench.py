@@ -473,26 +473,29 @@ def serve_arm(tc, gs, arcs, census_opts, rate, seconds, warmup, seed):
                             "max": float(max(t["gpu_ms"] for t in trace))} if trace else None}, results, rid_graph
 
 
-def serving_comparison(tc, torch, sh, model, args):
-    """Serving workload with the plain and the learned schedule: p50/p99 latency and arcs/s."""
+def serving_comparison(tc, torch, sh, model, args, algo):
+    """Serving workload with the plain and the learned schedule (the bench's kernel form):
+    p50/p99 latency and arcs/s, and a short sweep of higher arrival rates."""
     from paper_1209_6308_gb300 import learned
     t0 = time.perf_counter()
     pool = serving_pool()
     gen_s = time.perf_counter() - t0
     log(f"serving pool generated in {gen_s:.1f}s")
-    gs = [tc.Graph.from_arcs(n, s, d, stream=sh, options=learned.PLAIN) for (_, (n, s, d)) in pool]
+    plain = {"algo": algo}
+    learn = {"algo": algo, "schedule": tc.TC_SCHED_LEARNED}
+    gs = [tc.Graph.from_arcs(n, s, d, stream=sh, options=plain) for (_, (n, s, d)) in pool]
     arcs = [len(s) for (_, (_, s, _)) in pool]
-    want = [g.census(stream=sh, options=learned.PLAIN) for g in gs]
+    want = [g.census(stream=sh, options=plain) for g in gs]
     out = {"workload": SERVE_POOL + f"_poisson{int(args.serve_rate)}_seed5", "graphs": len(gs),
            "pool_arcs": int(sum(arcs)), "rate_per_s": args.serve_rate, "measured_s": args.serve_seconds,
            "warmup_s": args.serve_warmup, "quantum_us": 1000, "lanes": 3, "pool_generation_s": gen_s,
-           "selection": "graph i with probability proportional to 1/arcs_i"}
+           "selection": "graph i with probability proportional to 1/arcs_i", "kernel_form": FORM_NAMES[algo]}
     try:
-        arms = [("plain", learned.PLAIN)]
+        arms = [("plain", plain)]
         if model is not None:
             for g in gs:
                 learned.attach(model, g, stream=sh)
-            arms.append(("learned", learned.LEARNED))
+            arms.append(("learned", learn))
         exact = True
         for name, opts in arms:
             log(f"serving arm {name}")
@@ -505,7 +508,7 @@ def serving_comparison(tc, torch, sh, model, args):
         rates = [float(x) for x in args.serve_sweep.split(",") if x.strip()]
         for rate in rates:
             log(f"serving sweep at {rate:.0f} req/s")
-            m, res, rid_graph = serve_arm(tc, gs, arcs, learned.PLAIN, rate, args.sweep_seconds, 2.0, 6)
+            m, res, rid_graph = serve_arm(tc, gs, arcs, plain, rate, args.sweep_seconds, 2.0, 6)
             exact &= all(r.census() == want[rid_graph[r.id][1]] for r in res)
             sweep.append({"rate_per_s": rate, "measured_s": args.sweep_seconds, "warmup_s": 2.0,
                           **{k: m.get(k) for k in ("requests", "p50_ms", "p99_ms", "max_ms", "arcs_per_s",
@@ -809,7 +812,7 @@ def run_gpu(args):
     serve_line = None
     if not args.no_serve:
         log("serving")
-        serve_line = serving_comparison(tc, torch, sh, model, args)
+        serve_line = serving_comparison(tc, torch, sh, model, args, algo)
         log("serving done")
     if model is not None:
         tc.tc_costmodel_destroy(model)

@@ -61,7 +61,7 @@ typedef enum {
      * (a < b < c met once, walking the lower-id neighbours of c against those of b), whose
      * tricode fixes the triad and its corrections to the three pairs' bulk and dyadic
      * counts (steps 2.1.2 - 2.1.4).  Needs the per upper pair tables every built graph has;
-     * warp_max_deg <= 128.  Not offered by the server. */
+     * warp_max_deg <= 128. */
     TC_ALGO_TRIANGLE = 2
 } tc_algo;
 
@@ -334,7 +334,9 @@ tc_status tc_graph_attach_costmodel(tc_graph* g, const tc_costmodel* c, void* st
  * continuous batching: an engine thread runs each request as slices of its work items
  * (Fig. 5 step 2 pairs), up to 32 slices of different requests per launch ("wave") of the
  * census kernel, each wave sized to a target device time (at least the time of its heaviest
- * item).  New requests join the next wave; shortest remaining work goes first, and the oldest
+ * item).  In the TC_ALGO_TRIANGLE form a wave is the bulk pair sums and the triangle walk over
+ * the wave's slices, which add to each request's raw sums and tricode histogram, and, for
+ * the requests the wave finishes, one block each that folds those into the 16 counts.  New requests join the next wave; shortest remaining work goes first, and the oldest
  * request, once older than starve_ms, gets up to half of each wave.  With two or more lanes,
  * lane 0 runs the requests larger than half a quantum's work in waves that leave one CTA slot
  * per SM free, and the other lanes (high-priority streams) run the small ones in that slot.

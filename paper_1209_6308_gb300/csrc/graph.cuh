@@ -141,6 +141,13 @@ tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* item
 tc_status triangle_census_batch(const GraphDev* d_graphs, uint32_t k, const Item* items, uint32_t n_items,
                                 const uint4* wblocks, uint32_t n_wblocks, const Opts& o, uint32_t* ctr,
                                 unsigned long long* d_scratch, unsigned long long* d_out, cudaStream_t st);
+// Serving wave of the triangle form: the request slices' bulk sums and triangle tricodes into each
+// request's 96-uint64 scratch (WaveReq.out); ctr: 4 zeroed uint32.
+tc_status triangle_census_wave(const WaveReq* d_reqs, uint32_t n_reqs, uint32_t total_items, uint32_t total_blocks,
+                               const Opts& o, unsigned grid, uint32_t* ctr, cudaStream_t st);
+// Fold n finished requests' scratch into 16 counts each at d_dst + 16 k (index 0 = 0) and zero the
+// scratch.
+tc_status triangle_collect(unsigned long long* const* scratch, uint32_t n, unsigned long long* d_dst, cudaStream_t st);
 // The triangle walk alone: histogram of the 64 tricodes (old == nullptr) or of the 64 states in
 // the caller's id order (old = original id per vertex, d_perm_state = [9][64] state of a
 // tricode per rank pattern) of every triangle, added into d_hist64; ctr: 4 zeroed uint32.

@@ -50,8 +50,9 @@ uint64_t steady_ns() {
 constexpr uint64_t kPairUnits = 16;   // per-pair overhead in element units (offsets, the pair fold)
 
 // N[v] entries the census walks for the upper pair (u, v = N[u][j]): those past u when the
-// graph has per-pair tables, else all of N[v].
-__device__ __forceinline__ uint64_t walked(const GraphDev& g, uint32_t u, uint32_t j, uint32_t v) {
+// graph has per-pair tables, else all of N[v]; the triangle form walks those below u.
+__device__ __forceinline__ uint64_t walked(const GraphDev& g, uint32_t u, uint32_t j, uint32_t v, int algo) {
+    if (algo == TC_ALGO_TRIANGLE) return g.rp[g.ub[u] + (j - g.up[u])];
     const uint64_t dv = g.off[v + 1] - g.off[v];
     return g.rp ? dv - 1 - g.rp[g.ub[u] + (j - g.up[u])] : dv;
 }
@@ -70,7 +71,7 @@ __global__ void k_item_cost(GraphDev g, const Item* __restrict__ items, uint32_t
         unsigned long long c = 0;
         for (uint32_t j = it.j0 + lane; j < it.j1; j += 32) {
             const uint32_t v = g.adj[ub + j] >> 2;
-            c += walked(g, it.u, j, v) + kPairUnits + (algo == TC_ALGO_UNION ? du / 2 : 0);
+            c += walked(g, it.u, j, v, algo) + kPairUnits + (algo == TC_ALGO_UNION ? du / 2 : 0);
         }
         c = __reduce_add_sync(0xffffffffu, (unsigned)(c & 0xffffffffu)) +
             ((unsigned long long)__reduce_add_sync(0xffffffffu, (unsigned)(c >> 32)) << 32);
@@ -93,7 +94,8 @@ __global__ void k_block_cost(GraphDev g, uint32_t w0, uint32_t w1, uint32_t n_bl
             c = du;
             for (uint64_t j = ub + g.up[u]; j < ub + du; ++j) {
                 const uint32_t v = g.adj[j] >> 2;
-                c += walked(g, (uint32_t)u, (uint32_t)(j - ub), v) + kPairUnits + (algo == TC_ALGO_UNION ? du / 2 : 0);
+                c += walked(g, (uint32_t)u, (uint32_t)(j - ub), v, algo) + kPairUnits +
+                     (algo == TC_ALGO_UNION ? du / 2 : 0);
             }
         }
         c = __reduce_add_sync(0xffffffffu, (unsigned)(c & 0xffffffffu)) +
@@ -117,7 +119,7 @@ __global__ void k_pair_cost(GraphDev g, const Item* __restrict__ items, const ui
         const uint32_t j = w.j0 + (uint32_t)(p - pre[lo]);
         const uint64_t ub = g.off[w.u], du = g.off[w.u + 1] - ub;
         const uint32_t v = g.adj[ub + j] >> 2;
-        cost[p] = walked(g, w.u, j, v) + kPairUnits + ((du + chunk - 1) / chunk) * kPairUnits +
+        cost[p] = walked(g, w.u, j, v, algo) + kPairUnits + ((du + chunk - 1) / chunk) * kPairUnits +
                   (algo == TC_ALGO_UNION ? du / 2 : 0);
     }
 }
@@ -225,7 +227,8 @@ struct tc_server {
     // engine-owned
     std::vector<std::unique_ptr<tc::Req>> active;
     std::vector<uint32_t> free_slots;
-    tc::DevBuf slots;                    // [max_active][16] uint64
+    tc::DevBuf slots;                    // [max_active][slot_stride] uint64
+    uint32_t slot_stride = 16;           // 16 counters, or the triangle form's 96-uint64 scratch
     tc::Lane lanes[tc::kMaxLanes];
     std::thread engine;
 };
@@ -338,7 +341,7 @@ bool retire(tc_server* s) {
             for (Req* r : w->slices) {
                 if (r->status != TC_OK && r->left > 0 && r->inflight == 0) {
                     r->left = 0;
-                    cudaMemsetAsync(s->slots.as<unsigned long long>() + 16ull * r->slot, 0, 128, ln.st);
+                    cudaMemsetAsync(s->slots.as<unsigned long long>() + (uint64_t)s->slot_stride * r->slot, 0, 8ull * s->slot_stride, ln.st);
                     finish(s, r, nullptr, t_done, r->lane);
                     s->free_slots.push_back(r->slot);
                     fin = true;
@@ -476,7 +479,7 @@ void launch_wave(tc_server* s, int L) {
         WaveReq& d = w->h_desc[n];
         d.g = G.gd;
         d.items = G.items.as<Item>() + i0;
-        d.out = s->slots.as<unsigned long long>() + 16ull * r->slot;
+        d.out = s->slots.as<unsigned long long>() + (uint64_t)s->slot_stride * r->slot;
         d.n_items = i1 - i0;
         d.item_pre = tot_items;
         d.warp_begin = G.warp_begin + 32u * b0;
@@ -528,18 +531,27 @@ void launch_wave(tc_server* s, int L) {
     cudaError_t e = cudaMemcpyAsync(w->d_desc, w->h_desc, kDescBytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(w->e0, st);
     tc_status ks = TC_OK;
+    const bool tri = s->opts.algo == TC_ALGO_TRIANGLE;
     if (e == cudaSuccess)
-        ks = census_launch_wave(reinterpret_cast<const WaveReq*>(w->d_desc), n, tot_items, tot_blocks, s->opts, grid,
-                                reinterpret_cast<uint32_t*>(w->d_desc + zero_ctr_off), st);
+        ks = tri ? triangle_census_wave(reinterpret_cast<const WaveReq*>(w->d_desc), n, tot_items, tot_blocks, s->opts,
+                                        grid, reinterpret_cast<uint32_t*>(w->d_desc + zero_ctr_off), st)
+                 : census_launch_wave(reinterpret_cast<const WaveReq*>(w->d_desc), n, tot_items, tot_blocks, s->opts,
+                                      grid, reinterpret_cast<uint32_t*>(w->d_desc + zero_ctr_off), st);
     if (e == cudaSuccess && ks == TC_OK && !w->finishing.empty()) {
-        CollectArgs a;
-        std::memset(&a, 0, sizeof(a));
+        unsigned long long* src[kMaxWave];
         for (size_t k = 0; k < w->finishing.size(); ++k)
-            a.src[k] = s->slots.as<unsigned long long>() + 16ull * w->finishing[k]->slot;
-        a.dst = w->d_res;
-        a.n = (uint32_t)w->finishing.size();
-        k_collect<<<1, 16 * kMaxWave, 0, st>>>(a);
-        e = cudaGetLastError();
+            src[k] = s->slots.as<unsigned long long>() + (uint64_t)s->slot_stride * w->finishing[k]->slot;
+        if (tri) {
+            ks = triangle_collect(src, (uint32_t)w->finishing.size(), w->d_res, st);
+        } else {
+            CollectArgs a;
+            std::memset(&a, 0, sizeof(a));
+            for (size_t k = 0; k < w->finishing.size(); ++k) a.src[k] = src[k];
+            a.dst = w->d_res;
+            a.n = (uint32_t)w->finishing.size();
+            k_collect<<<1, 16 * kMaxWave, 0, st>>>(a);
+            e = cudaGetLastError();
+        }
     }
     if (e == cudaSuccess && ks == TC_OK) e = cudaEventRecord(w->e1, st);
     if (e != cudaSuccess || ks != TC_OK) {
@@ -555,7 +567,7 @@ void launch_wave(tc_server* s, int L) {
         const uint64_t t = steady_ns();
         for (Req* r : w->slices) {
             if (r->inflight == 0) {
-                cudaMemsetAsync(s->slots.as<unsigned long long>() + 16ull * r->slot, 0, 128, st);
+                cudaMemsetAsync(s->slots.as<unsigned long long>() + (uint64_t)s->slot_stride * r->slot, 0, 8ull * s->slot_stride, st);
                 finish(s, r, nullptr, t, r->lane);
                 s->free_slots.push_back(r->slot);
             }
@@ -637,7 +649,6 @@ tc_status tc_server_create(const tc_server_options* opt, tc_server** out) {
     if (o.lanes > (uint32_t)kMaxLanes) return fail(TC_ERR_ARG, "lanes must be <= 4");
     std::unique_ptr<tc_server> s(new tc_server());
     TC_TRY(resolve_opts(&o.census, nullptr, &s->opts));
-    if (s->opts.algo == TC_ALGO_TRIANGLE) return fail(TC_ERR_ARG, "the server runs the union or suffix form");
     if (s->opts.schedule != TC_SCHED_PLAIN && s->opts.schedule != TC_SCHED_LEARNED)
         return fail(TC_ERR_ARG, "unknown schedule");
     s->max_active = o.max_active ? o.max_active : 1024;
@@ -655,7 +666,8 @@ tc_status tc_server_create(const tc_server_options* opt, tc_server** out) {
     s->grid_bulk = s->opts.ctas_per_sm > 1 ? sms * (s->opts.ctas_per_sm - 1) : sms;
     int prio_lo = 0, prio_hi = 0;
     TC_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-    TC_TRY(s->slots.alloc_persistent(sizeof(unsigned long long) * 16ull * s->max_active));
+    s->slot_stride = s->opts.algo == TC_ALGO_TRIANGLE ? 96u : 16u;
+    TC_TRY(s->slots.alloc_persistent(sizeof(unsigned long long) * (uint64_t)s->slot_stride * s->max_active));
     TC_CUDA(cudaMemset(s->slots.p, 0, s->slots.bytes));
     for (uint32_t i = 0; i < s->max_active; ++i) s->free_slots.push_back(s->max_active - 1 - i);
     bool ok = true;
@@ -677,7 +689,7 @@ tc_status tc_server_create(const tc_server_options* opt, tc_server** out) {
         tc_server_destroy(s.release());
         return cuda_fail(e == cudaSuccess ? cudaErrorMemoryAllocation : e, "server streams and wave buffers");
     }
-    const tc_status ps = census_prepare(s->lanes[0].st, s->opts);
+    const tc_status ps = s->opts.algo == TC_ALGO_TRIANGLE ? TC_OK : census_prepare(s->lanes[0].st, s->opts);
     if (ps != TC_OK) {
         const std::string why = tc_last_error();
         tc_server_destroy(s.release());

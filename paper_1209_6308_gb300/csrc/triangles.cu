@@ -67,11 +67,29 @@ struct TriParams {
     const GraphDev* graphs;
     const uint4* wblocks;
     uint32_t n_wblocks;
+    // serving wave: n_items / n_wblocks are the wave's totals over its request slices
+    const WaveReq* reqs;
+    uint32_t n_reqs;
 };
 
 // batched triangle form: per graph 96 uint64 of scratch, the 21 bulk sums at [0, 21) and the 64
-// triangle tricodes at [32, 96)
+// triangle tricodes at [32, 96); a serving wave's requests have the same scratch at WaveReq.out
 constexpr uint32_t kBatchStride = 96;
+
+// launch modes: one graph; a batch of graphs (items tagged with the graph, blocks (u0, u1, g));
+// a serving wave (slices of several requests, descriptors in global memory)
+enum { kTriSingle = 0, kTriBatch = 1, kTriWave = 2 };
+
+// index r of the last request whose prefix is <= i (prefixes ascend from 0)
+template <typename F>
+__device__ __forceinline__ uint32_t find_req(uint32_t count, uint32_t i, F pre) {
+    uint32_t lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre(mid) <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
 
 // Walk, for the pairs (b, c = N[b][j]), j in [j0, j1), 32 pairs per batch, the entries of N[c]
 // below b (rp = b's position in N[c], from the pair tables; pb + j indexes the pair) and count
@@ -200,7 +218,7 @@ __device__ __forceinline__ void flush_warp_hist(uint32_t* myHist, unsigned long 
     __syncwarp();
 }
 
-template <bool OLD, bool BATCH>
+template <bool OLD, int MODE>
 __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t slots = 2u * P.chunk;
@@ -225,8 +243,13 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
     auto use_graph = [&](uint32_t gi) {
         if (cur_graph != 0xffffffffu) flush_warp_hist(myHist, ghist, lane);
         cur_graph = gi;
-        G = P.graphs[gi];
-        ghist = P.hist + (uint64_t)kBatchStride * gi;
+        if (MODE == kTriWave) {
+            G = P.reqs[gi].g;
+            ghist = P.reqs[gi].out + 32;
+        } else {
+            G = P.graphs[gi];
+            ghist = P.hist + (uint64_t)kBatchStride * gi;
+        }
     };
     uint32_t since_flush = 0;   // warp-uniform: entries walked since this warp's bins were flushed
     // the hash region (2 x chunk words) holds a direct map of 32 x chunk ids at two bits each
@@ -238,8 +261,15 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
         __syncthreads();
         const uint32_t it = s_item;
         if (it >= P.n_items) break;
-        const Item w = P.items[it];
-        if (BATCH && w.pad != cur_graph) use_graph(w.pad);
+        Item w;
+        if (MODE == kTriWave) {
+            const uint32_t r = find_req(P.n_reqs, it, [&](uint32_t q) { return P.reqs[q].item_pre; });
+            w = P.reqs[r].items[it - P.reqs[r].item_pre];
+            if (r != cur_graph) use_graph(r);
+        } else {
+            w = P.items[it];
+            if (MODE == kTriBatch && w.pad != cur_graph) use_graph(w.pad);
+        }
         const long long t0 = clock64();
         const uint32_t b = w.u;
         const uint64_t bbase = G.off[b];
@@ -307,7 +337,17 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
     uint32_t* wO = sWO + (OLD ? warp * kWarpSlots : 0u);
     for (;;) {
         uint32_t b0, b1;
-        if (BATCH) {
+        if (MODE == kTriWave) {
+            uint32_t bk = 0;
+            if (lane == 0) bk = atomicAdd(&P.ctr[1], 1u);
+            bk = __shfl_sync(0xffffffffu, bk, 0);
+            if (bk >= P.n_wblocks) break;
+            const uint32_t r = find_req(P.n_reqs, bk, [&](uint32_t q) { return P.reqs[q].block_pre; });
+            if (r != cur_graph) use_graph(r);
+            const WaveReq& q = P.reqs[r];
+            b0 = q.warp_begin + ((bk - q.block_pre) << q.pad);
+            b1 = min(b0 + (1u << q.pad), q.warp_end);
+        } else if (MODE == kTriBatch) {
             uint32_t bk = 0;
             if (lane == 0) bk = atomicAdd(&P.ctr[1], 1u);
             bk = __shfl_sync(0xffffffffu, bk, 0);
@@ -349,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
             }
         }
     }
-    if (!BATCH || cur_graph != 0xffffffffu) flush_warp_hist(myHist, ghist, lane);
+    if (MODE == kTriSingle || cur_graph != 0xffffffffu) flush_warp_hist(myHist, ghist, lane);
 }
 
 // One pair's bulk sums into acc (see k_pair_bulk): u of degree du, the pair's entry e = N[u][j]
@@ -379,7 +419,9 @@ __device__ __forceinline__ void bulk_pair(const GraphDev& g, unsigned long long 
 // one vertex each, a warp per item), then the one-warp vertices in blocks of 32 consecutive
 // ones, whose upper pairs are consecutive in the table order and are walked as one flattened
 // range.  Work comes from the counters ctr[2] (items) and ctr[3] (blocks), zeroed by the caller.
-// BATCH: item.pad and the blocks' third field name the graph (graphs[g], sums at raw + kBatchStride g).
+// Batched: item.pad and the blocks' third field name the graph (graphs[g], sums at raw +
+// kBatchStride g); serving wave: request slices as in the census kernel's wave mode (sums at
+// the request's scratch, WaveReq.out).
 struct BulkParams {
     GraphDev g;
     const Item* items;
@@ -388,6 +430,8 @@ struct BulkParams {
     const GraphDev* graphs;       // batched
     const uint4* wblocks;
     uint32_t n_wblocks;
+    const WaveReq* reqs;          // serving wave (n_items, n_wblocks: the wave's totals)
+    uint32_t n_reqs;
     uint32_t* ctr;
     unsigned long long* raw;
 };
@@ -404,7 +448,7 @@ __device__ __forceinline__ void flush_bulk(unsigned long long (&acc)[3][7], unsi
         }
 }
 
-template <bool BATCH>
+template <int MODE>
 __global__ void __launch_bounds__(256, 4) k_pair_bulk(BulkParams P) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t le_mask = (2u << lane) - 1u;
@@ -419,8 +463,13 @@ __global__ void __launch_bounds__(256, 4) k_pair_bulk(BulkParams P) {
     auto use_graph = [&](uint32_t gi) {
         if (cur_graph != 0xffffffffu) flush_bulk(acc, raw, lane);
         cur_graph = gi;
-        G = P.graphs[gi];
-        raw = P.raw + (uint64_t)kBatchStride * gi;
+        if (MODE == kTriWave) {
+            G = P.reqs[gi].g;
+            raw = P.reqs[gi].out;
+        } else {
+            G = P.graphs[gi];
+            raw = P.raw + (uint64_t)kBatchStride * gi;
+        }
     };
     // the CTA items, a warp each
     for (;;) {
@@ -428,8 +477,15 @@ __global__ void __launch_bounds__(256, 4) k_pair_bulk(BulkParams P) {
         if (lane == 0) it = atomicAdd(&P.ctr[2], 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= P.n_items) break;
-        const Item w = P.items[it];
-        if (BATCH && w.pad != cur_graph) use_graph(w.pad);
+        Item w;
+        if (MODE == kTriWave) {
+            const uint32_t r = find_req(P.n_reqs, it, [&](uint32_t q) { return P.reqs[q].item_pre; });
+            w = P.reqs[r].items[it - P.reqs[r].item_pre];
+            if (r != cur_graph) use_graph(r);
+        } else {
+            w = P.items[it];
+            if (MODE == kTriBatch && w.pad != cur_graph) use_graph(w.pad);
+        }
         const unsigned long long n = G.n;
         const uint64_t ubase = G.off[w.u];
         const uint32_t du = (uint32_t)(G.off[w.u + 1] - ubase);
@@ -442,7 +498,14 @@ __global__ void __launch_bounds__(256, 4) k_pair_bulk(BulkParams P) {
         if (lane == 0) blk = atomicAdd(&P.ctr[3], 1u);
         blk = __shfl_sync(0xffffffffu, blk, 0);
         uint64_t base, end;
-        if (BATCH) {
+        if (MODE == kTriWave) {
+            if (blk >= P.n_wblocks) break;
+            const uint32_t r = find_req(P.n_reqs, blk, [&](uint32_t q) { return P.reqs[q].block_pre; });
+            if (r != cur_graph) use_graph(r);
+            const WaveReq& q = P.reqs[r];
+            base = q.warp_begin + ((uint64_t)(blk - q.block_pre) << q.pad);
+            end = base + (1u << q.pad) < q.warp_end ? base + (1u << q.pad) : q.warp_end;
+        } else if (MODE == kTriBatch) {
             if (blk >= P.n_wblocks) break;
             const uint4 wbk = P.wblocks[blk];
             if (wbk.z != cur_graph) use_graph(wbk.z);
@@ -495,7 +558,7 @@ __global__ void __launch_bounds__(256, 4) k_pair_bulk(BulkParams P) {
             bulk_pair(G, n, sD, j, G.adj[sB + j], pstart + i, acc);
         }
     }
-    if (!BATCH || cur_graph != 0xffffffffu) flush_bulk(acc, raw, lane);
+    if (MODE == kTriSingle || cur_graph != 0xffffffffu) flush_bulk(acc, raw, lane);
 }
 
 struct Table64 {
@@ -543,7 +606,47 @@ __global__ void k_tri_fold(const unsigned long long* __restrict__ raw, const uns
     if (t >= 1 && t < 16 && s[t]) atomicAdd(&out16[t], s[t]);
 }
 
-std::atomic<uint64_t> g_tri_attr[3] = {};
+// Serving: fold each finished request's scratch (block r) into its 16 counts in mapped host
+// memory (dst + 16 r, index 0 = 0) and zero the scratch for the slot's next request.
+struct TriCollect {
+    unsigned long long* src[kMaxWave];
+    unsigned long long* dst;
+    uint32_t n;
+};
+
+__global__ void k_tri_collect(TriCollect a, Table64 T) {
+    __shared__ unsigned long long out[16];
+    const uint32_t r = blockIdx.x, t = threadIdx.x;
+    if (r >= a.n) return;
+    if (t < 16) out[t] = 0ull;
+    __syncthreads();
+    unsigned long long* sc = a.src[r];
+    // the same fold as k_tri_fold, into shared memory
+    if (t < 21) {
+        const uint32_t c = t / 7 + 1, k = t % 7;
+        const unsigned long long v = sc[t];
+        const uint32_t cls = k < 3 ? T.t[c | ((k + 1) << 2)] : (k < 6 ? T.t[c | ((k - 2) << 4)] : (c == 3u ? 2u : 1u));
+        if (v) atomicAdd(&out[cls], v);
+    }
+    const unsigned long long h = sc[32 + t];
+    if (h) {
+        const uint32_t cab = t & 3u, dac = (t >> 4) & 3u, dbc = (t >> 2) & 3u;
+        const uint32_t dcb = ((dbc & 1u) << 1) | (dbc >> 1), cac = ((dac & 1u) << 1) | (dac >> 1);
+        const unsigned long long m = 0ull - h;
+        atomicAdd(&out[T.t[t]], h);
+        atomicAdd(&out[T.t[cab | (dac << 4)]], m);
+        atomicAdd(&out[T.t[cab | (dbc << 2)]], m);
+        atomicAdd(&out[T.t[cac | (dcb << 2)]], m);
+        atomicAdd(&out[cab == 3u ? 2u : 1u], h);
+        atomicAdd(&out[dac == 3u ? 2u : 1u], h);
+        atomicAdd(&out[dbc == 3u ? 2u : 1u], h);
+    }
+    __syncthreads();
+    if (t < 16) a.dst[16 * r + t] = t ? out[t] : 0ull;
+    for (uint32_t k = t; k < kBatchStride; k += blockDim.x) sc[k] = 0ull;
+}
+
+std::atomic<uint64_t> g_tri_attr[4] = {};
 
 size_t tri_smem(uint32_t chunk, bool old) {
     const size_t slots = 2ull * chunk;
@@ -551,13 +654,13 @@ size_t tri_smem(uint32_t chunk, bool old) {
            (old ? 9 * 64 : 0);
 }
 
-// form: 0 single graph, 1 caller-id states (64-state census), 2 batched
+// form: 0 single graph, 1 caller-id states (64-state census), 2 batched, 3 serving wave
 tc_status tri_prepare(int form, size_t smem) {
     int dev = 0;
     TC_CUDA(cudaGetDevice(&dev));
     const uint64_t bit = 1ull << (dev & 63);
-    const void* fns[3] = {(const void*)k_triangles<false, false>, (const void*)k_triangles<true, false>,
-                          (const void*)k_triangles<false, true>};
+    const void* fns[4] = {(const void*)k_triangles<false, kTriSingle>, (const void*)k_triangles<true, kTriSingle>,
+                          (const void*)k_triangles<false, kTriBatch>, (const void*)k_triangles<false, kTriWave>};
     const void* fn = fns[form];
     int optin = 0;
     TC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -602,8 +705,8 @@ tc_status triangles_launch(const GraphDev& gd, const Opts& o, const Item* items,
     P.hist = d_hist64;
     P.vcost = d_vcost;
     const unsigned grid = (unsigned)census_grid(o);
-    if (is_old) k_triangles<true, false><<<grid, kThreads, smem, st>>>(P);
-    else k_triangles<false, false><<<grid, kThreads, smem, st>>>(P);
+    if (is_old) k_triangles<true, kTriSingle><<<grid, kThreads, smem, st>>>(P);
+    else k_triangles<false, kTriSingle><<<grid, kThreads, smem, st>>>(P);
     TC_LAUNCH("k_triangles");
     return TC_OK;
 }
@@ -630,7 +733,7 @@ tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* item
         B.we = warp_end;
         B.ctr = g.ctr.as<uint32_t>();
         B.raw = raw;
-        k_pair_bulk<false><<<grid_for(units * 32, 256, 4u * (unsigned)sm_count()), 256, 0, st>>>(B);
+        k_pair_bulk<kTriSingle><<<grid_for(units * 32, 256, 4u * (unsigned)sm_count()), 256, 0, st>>>(B);
         TC_LAUNCH("k_pair_bulk");
     }
     TC_TRY(triangles_launch(gd, o, items, n_items, warp_begin, warp_end, g.ctr.as<uint32_t>(), nullptr, nullptr, hist,
@@ -660,7 +763,7 @@ tc_status triangle_census_batch(const GraphDev* d_graphs, uint32_t k, const Item
         B.n_wblocks = n_wblocks;
         B.ctr = ctr;
         B.raw = d_scratch;
-        k_pair_bulk<true><<<grid_for(units * 32, 256, 4u * (unsigned)sm_count()), 256, 0, st>>>(B);
+        k_pair_bulk<kTriBatch><<<grid_for(units * 32, 256, 4u * (unsigned)sm_count()), 256, 0, st>>>(B);
         TC_LAUNCH("k_pair_bulk (batched)");
         TriParams P;
         std::memset(&P, 0, sizeof(P));
@@ -672,13 +775,56 @@ tc_status triangle_census_batch(const GraphDev* d_graphs, uint32_t k, const Item
         P.graphs = d_graphs;
         P.wblocks = wblocks;
         P.n_wblocks = n_wblocks;
-        k_triangles<false, true><<<(unsigned)census_grid(o), kThreads, smem, st>>>(P);
+        k_triangles<false, kTriBatch><<<(unsigned)census_grid(o), kThreads, smem, st>>>(P);
         TC_LAUNCH("k_triangles (batched)");
     }
     Table64 T;
     TC_TRY(fold_table(&T));
     k_tri_fold<<<k, 64, 0, st>>>(d_scratch, d_scratch + 32, T, d_out);
     TC_LAUNCH("k_tri_fold (batched)");
+    return TC_OK;
+}
+
+tc_status triangle_census_wave(const WaveReq* d_reqs, uint32_t n_reqs, uint32_t total_items, uint32_t total_blocks,
+                               const Opts& o, unsigned grid, uint32_t* ctr, cudaStream_t st) {
+    if (n_reqs > kMaxWave) return fail(TC_ERR_RANGE, "wave larger than kMaxWave requests");
+    const size_t smem = tri_smem(o.chunk, false);
+    TC_TRY(tri_prepare(3, smem));
+    BulkParams B;
+    std::memset(&B, 0, sizeof(B));
+    B.n_items = total_items;
+    B.n_wblocks = total_blocks;
+    B.reqs = d_reqs;
+    B.n_reqs = n_reqs;
+    B.ctr = ctr;
+    const uint64_t units = (uint64_t)total_items + total_blocks;
+    k_pair_bulk<kTriWave><<<grid_for(units * 32, 256, 4u * (unsigned)sm_count()), 256, 0, st>>>(B);
+    TC_LAUNCH("k_pair_bulk (wave)");
+    TriParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.n_items = total_items;
+    P.n_wblocks = total_blocks;
+    P.reqs = d_reqs;
+    P.n_reqs = n_reqs;
+    P.chunk = o.chunk;
+    P.ctr = ctr;
+    k_triangles<false, kTriWave><<<grid, kThreads, smem, st>>>(P);
+    TC_LAUNCH("k_triangles (wave)");
+    return TC_OK;
+}
+
+tc_status triangle_collect(unsigned long long* const* scratch, uint32_t n, unsigned long long* d_dst, cudaStream_t st) {
+    if (n == 0) return TC_OK;
+    if (n > kMaxWave) return fail(TC_ERR_RANGE, "more finished requests than a wave holds");
+    TriCollect a;
+    std::memset(&a, 0, sizeof(a));
+    for (uint32_t k = 0; k < n; ++k) a.src[k] = scratch[k];
+    a.dst = d_dst;
+    a.n = n;
+    Table64 T;
+    TC_TRY(fold_table(&T));
+    k_tri_collect<<<n, 64, 0, st>>>(a, T);
+    TC_LAUNCH("k_tri_collect");
     return TC_OK;
 }
 

@@ -87,12 +87,13 @@ def test_oracle_agrees_with_the_standalone_census_on_small_pool_graphs(tc, pool)
             assert want[k] == oracle.census_bm(n, s, d), k
 
 
-def test_mixed_requests_equal_standalone_census(tc, pool):
+@pytest.mark.parametrize("form", [1, 2])
+def test_mixed_requests_equal_standalone_census(tc, pool, form):
     gs, want, _ = pool
     rng = np.random.default_rng(11)
     order = list(rng.integers(0, len(gs), 300))
     # a short quantum forces large censuses into many slices shared with other requests
-    res, rid_graph, ids, stats = _serve(tc, gs, order, {"quantum_us": 40, "lanes": 2})
+    res, rid_graph, ids, stats = _serve(tc, gs, order, {"quantum_us": 40, "lanes": 2}, census={"algo": form})
     assert len(res) == len(order)
     assert stats["completed"] == len(order) and stats["error"] == 0
     for r in res:
@@ -105,11 +106,11 @@ def test_mixed_requests_equal_standalone_census(tc, pool):
     assert stats["slices"] > stats["waves"]        # waves mixed requests
 
 
-@pytest.mark.parametrize("lanes,quantum", [(1, 1000), (4, 200), (3, 5)])
-def test_lane_and_quantum_settings_keep_counts(tc, pool, lanes, quantum):
+@pytest.mark.parametrize("lanes,quantum,form", [(1, 1000, 1), (4, 200, 1), (3, 5, 1), (1, 1000, 2), (3, 5, 2)])
+def test_lane_and_quantum_settings_keep_counts(tc, pool, lanes, quantum, form):
     gs, want, _ = pool
     order = [k % len(gs) for k in range(3 * len(gs))]
-    res, rid_graph, _, stats = _serve(tc, gs, order, {"quantum_us": quantum, "lanes": lanes})
+    res, rid_graph, _, stats = _serve(tc, gs, order, {"quantum_us": quantum, "lanes": lanes}, census={"algo": form})
     assert sorted(rid_graph) == sorted(r.id for r in res)
     for r in res:
         assert r.census() == want[rid_graph[r.id]]
@@ -120,9 +121,10 @@ def test_split_work_items_keep_counts(tc, pool):
     """A tiny item cap cuts every hub item into many pair ranges (each restaging N[u])."""
     gs, want, _ = pool
     order = list(range(len(gs))) * 2
-    res, rid_graph, ids, _ = _serve(tc, gs, order, {"quantum_us": 200, "max_item_units": 1})
-    for r in res:
-        assert r.census() == want[rid_graph[r.id]]
+    for form in (1, 2):
+        res, rid_graph, ids, _ = _serve(tc, gs, order, {"quantum_us": 200, "max_item_units": 1}, census={"algo": form})
+        for r in res:
+            assert r.census() == want[rid_graph[r.id]], form
     with tc.Server({"max_item_units": 1}, SUFFIX) as srv, tc.Server(None, SUFFIX) as ref:
         gid, rid = srv.add(gs[6]), ref.add(gs[6])             # R-MAT scale 16
         split_items = tc.tc_server_graph_units(srv.handle, gid)[1]
@@ -156,10 +158,11 @@ def test_learned_schedule_server(tc, pool):
         for g in gs:
             tc.tc_graph_attach_costmodel(g.handle, model)
         order = list(range(len(gs))) * 3
-        res, rid_graph, _, _ = _serve(tc, gs, order, {"quantum_us": 100},
-                                      census={"algo": 1, "schedule": tc.TC_SCHED_LEARNED})
-        for r in res:
-            assert r.census() == want[rid_graph[r.id]]
+        for form in (1, 2):
+            res, rid_graph, _, _ = _serve(tc, gs, order, {"quantum_us": 100},
+                                          census={"algo": form, "schedule": tc.TC_SCHED_LEARNED})
+            for r in res:
+                assert r.census() == want[rid_graph[r.id]], form
     finally:
         tc.tc_costmodel_destroy(model)
 
