@@ -376,8 +376,11 @@ def learned_comparison(tc, g, stream, model, info, reps, algo):
     plain_ms, plain_c = learned.census_ms(g, plain, stream, reps=reps)
     learned_ms, learned_c = learned.census_ms(g, learn, stream, reps=reps)
     q = learned.prediction_quality(model, g, options=plain, stream=stream.cuda_stream)
+    bal_plain = learned.balance(g, plain, stream=stream.cuda_stream)
+    bal_learned = learned.balance(g, learn, stream=stream.cuda_stream)
     return {"_plain_counts": plain_c, "training": info, "plain_ms": plain_ms, "learned_ms": learned_ms, "reps": reps,
             "speedup": plain_ms / learned_ms, "counts_identical": plain_c == learned_c,
+            "balance_plain": bal_plain, "balance_learned": bal_learned,
             "plain_arcs_per_s": None, "learned_arcs_per_s": None,
             "roofline_plain": form_roofline(tc, g.n, g.stats(), algo, plain_ms),
             "roofline_learned": form_roofline(tc, g.n, g.stats(), algo, learned_ms),
@@ -526,31 +529,59 @@ def serving_comparison(tc, torch, sh, model, args, algo):
     return out
 
 
-def interval_comparison(tc, torch, s, d, n, sh, name):
+def interval_comparison(tc, torch, s, d, n, sh, name, window=200, every=10):
     """Interval census (the paper's monitoring use): the bench graph's arcs in a random order at
-    uniform times over [0, 1000), a window of 200, a census every 100 from 200 to 1000; each
-    census builds the window's graph on the device and counts it (about a fifth of the arcs)."""
+    uniform times over [0, 1000), a window of 200, a census every 10 from 200 to 1000.  Each
+    census merges the arcs that entered and left since the last one into the window's kept arc
+    set, builds the window's graph from it and counts it (about a fifth of the arcs per window,
+    a twentieth of those changed per step).  Beside it, every tenth window rebuilt from its arcs
+    with tc_graph_create_arcs (device arrays) and counted, as a census without the kept set
+    would; both must give the same counts."""
     import numpy as np
     rng = np.random.default_rng(7)
     perm = rng.permutation(len(s))
     t = np.sort(rng.integers(0, 1000, len(s))).astype(np.uint64)
     src, dst = s[perm], d[perm]
-    times, windows = [], []
-    with tc.Stream(n, 200, options={"algo": tc.TC_ALGO_TRIANGLE}, stream=sh) as st:
+    opts = {"algo": tc.TC_ALGO_TRIANGLE}
+    times, windows, got = [], [], {}
+    with tc.Stream(n, window, options=opts, stream=sh) as st:
         t0 = time.perf_counter()
         st.push(src, dst, t)
         push_s = time.perf_counter() - t0
-        for t_now in range(200, 1001, 100):
+        for t_now in range(window, 1001, every):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            _, m = st.census(t_now)
+            c, m = st.census(t_now)
             times.append((time.perf_counter() - t1) * 1e3)
             windows.append(m)
-    ms = statistics.median(times)
-    return {"workload": name + "_times_uniform1000_window200_every100", "censuses": len(times),
+            got[t_now] = c
+        info = st.stats()
+    sd = torch.from_numpy(src.view("int32")).cuda()
+    dd = torch.from_numpy(dst.view("int32")).cuda()
+    full_times, same = [], True
+    for t_now in range(window, 1001, 10 * every):
+        a = int(np.searchsorted(t, t_now - window, side="right"))
+        b = int(np.searchsorted(t, t_now, side="right"))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h = tc.tc_graph_create_arcs(n, sd[a:b], dd[a:b], stream=sh, options=opts)
+        c = tc.tc_census(h, stream=sh, options=opts)
+        full_times.append((time.perf_counter() - t1) * 1e3)
+        tc.tc_graph_destroy(h)
+        same = same and c == got[t_now]
+    del sd, dd
+    ms = statistics.median(times[1:])
+    full_ms = statistics.median(full_times)
+    return {"workload": f"{name}_times_uniform1000_window{window}_every{every}", "censuses": len(times),
             "arcs_per_window_median": int(statistics.median(windows)), "ms_per_census_median": ms,
-            "arcs_per_s": statistics.median(windows) / (ms * 1e-3), "push_s": push_s,
-            "note": "per census: window graph build (sort, dedupe, relabel, CSR, tables) + census + D2H of 16 counts"}
+            "first_census_ms": times[0], "arcs_per_s": statistics.median(windows) / (ms * 1e-3), "push_s": push_s,
+            "set_rebuilds": info["rebuilds"], "set_repairs": info["repairs"],
+            "arcs_changed_last_census": info["last_added"] + info["last_evicted"],
+            "rebuild_from_arcs_ms_median": full_ms, "speedup_vs_rebuild": full_ms / ms,
+            "counts_identical_to_rebuild": same,
+            "note": "per census: merge of the entering and leaving arcs into the kept arc set, the window's "
+                    "graph from it (pairs, degrees, relabel, CSR, tables), census, D2H of 16 counts; "
+                    "wall time of the synchronous call"}
 
 
 def census64_comparison(tc, torch, sh, scale, steps=3):

@@ -151,7 +151,8 @@ tc_status tc_census_async(tc_graph* g, void* stream, const tc_options* opt, uint
  * smaller endpoint of its pairs, Fig. 5 step 2) added into d_vcost[n] (device uint64, indexed
  * by the relabelled id of tc_graph_device_csr; the caller zeroes it).  d_phase (device uint64,
  * may be NULL) receives, for each of the tc_census_grid() CTAs, the global timer in ns at
- * its start, at the end of its CTA work items and at its end.  Does not synchronise. */
+ * its start, at the end of its CTA work items and at its end (in the TC_ALGO_TRIANGLE form,
+ * those of the triangle walk's launch).  Does not synchronise. */
 tc_status tc_census_profile(tc_graph* g, void* stream, const tc_options* opt, uint64_t* d_out16,
                             uint64_t* d_vcost, uint64_t* d_phase);
 
@@ -428,8 +429,11 @@ void tc_server_destroy(tc_server* s);
  * a sliding window (the paper's monitoring application, Sec. 3: the census at fixed intervals).
  * The census at time t covers the arcs with t - window < time <= t, as a set (self-loops and
  * repeated arcs dropped) on the n vertices; it is exactly tc_census of those arcs.  The arcs of
- * the window stay on the device; each census builds that window's graph there and counts it.
- * Not thread-safe: one caller at a time per stream. */
+ * the window stay on the device, and so does the window's arc set between censuses (its
+ * distinct arcs, sorted, with their multiplicities): a census updates the set with the arcs
+ * that entered and left the window since the last one (a sort of those only and a merge), then
+ * builds the window's graph from the set and counts it.  Not thread-safe: one caller at a time
+ * per stream. */
 typedef struct tc_stream tc_stream;
 /* window > 0 in the caller's time unit; opt (may be NULL) as for tc_graph_create_arcs and
  * tc_census; `stream` is the CUDA stream every copy, build and census of this object uses. */
@@ -441,11 +445,22 @@ tc_status tc_stream_push(tc_stream* s, uint64_t m, const uint32_t* src, const ui
 /* Census of the window ending at t_now (Fig. 5, out as for tc_census); *arcs_in_window (may be
  * NULL) receives the number of arcs pushed into the window, before loops and repeats are
  * dropped.  t_now must not decrease across calls (TC_ERR_ARG): arcs older than the window are
- * freed after each census.  Synchronises the stream. */
+ * freed once the window's arc set is updated, even if the build or the count then fails.
+ * Synchronises the stream. */
 tc_status tc_stream_census(tc_stream* s, uint64_t t_now, tc_u128 out[16], uint64_t* arcs_in_window);
-/* Arcs held (pushed and not yet older than the last census's window), device capacity in
- * arcs, and censuses taken; any pointer may be NULL. */
-tc_status tc_stream_stats(const tc_stream* s, uint64_t* live_arcs, uint64_t* capacity, uint64_t* censuses);
+typedef struct {
+    uint64_t live_arcs;      /* arcs held: pushed and not older than the last census's window */
+    uint64_t capacity;       /* device capacity in arcs */
+    uint64_t censuses;       /* censuses taken */
+    uint64_t distinct_arcs;  /* distinct arcs (loops excluded) in the last census's window */
+    uint64_t rebuilds;       /* censuses that made the arc set from the whole window (the first,
+                                and any whose change was as large as the window) */
+    uint64_t repairs;        /* updates that found the set disagreeing with the window and made
+                                it afresh (0 unless something is wrong) */
+    uint64_t last_added;     /* arcs keyed as entering by the last census */
+    uint64_t last_evicted;   /* arcs keyed as leaving by the last census */
+} tc_stream_info;
+tc_status tc_stream_stats(const tc_stream* s, tc_stream_info* info);
 void tc_stream_destroy(tc_stream* s);
 
 /* The 64-entry tricode -> class table the kernels use (for inspection and tests). */

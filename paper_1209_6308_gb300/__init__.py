@@ -97,6 +97,11 @@ class tc_wave_record(ctypes.Structure):
         return {k: (float(getattr(self, k)) if k == "gpu_ms" else int(getattr(self, k))) for k, _ in self._fields_}
 
 
+class tc_stream_info(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("live_arcs", "capacity", "censuses", "distinct_arcs", "rebuilds",
+                                               "repairs", "last_added", "last_evicted")]
+
+
 _lib = None
 _VP, _U32, _U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
 
@@ -162,7 +167,7 @@ SIGNATURES = {
     "tc_stream_create": (ctypes.c_int, [_U32, _U64, _VP, _VP, ctypes.POINTER(_VP)]),
     "tc_stream_push": (ctypes.c_int, [_VP, _U64, _VP, _VP, _VP]),
     "tc_stream_census": (ctypes.c_int, [_VP, _U64, ctypes.POINTER(tc_u128), ctypes.POINTER(_U64)]),
-    "tc_stream_stats": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
+    "tc_stream_stats": (ctypes.c_int, [_VP, _VP]),
     "tc_stream_destroy": (None, [_VP]),
     "tc_tricode_table": (None, [ctypes.POINTER(ctypes.c_uint8)]),
 }
@@ -696,10 +701,9 @@ class Stream:
         return [out[i].value() for i in range(16)], int(m.value)
 
     def stats(self) -> dict:
-        a, b, c = _U64(), _U64(), _U64()
-        _check(load().tc_stream_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
-               "tc_stream_stats")
-        return {"live_arcs": int(a.value), "capacity": int(b.value), "censuses": int(c.value)}
+        info = tc_stream_info()
+        _check(load().tc_stream_stats(self.handle, ctypes.byref(info)), "tc_stream_stats")
+        return {f: int(getattr(info, f)) for f, _ in tc_stream_info._fields_}
 
     def close(self):
         if self.handle:

@@ -262,6 +262,36 @@ tc_status tc_graph_create_arcs(uint32_t n, uint64_t m, const uint32_t* src, cons
     return TC_OK;
 }
 
+}  // extern "C"
+
+namespace tc {
+
+tc_status graph_create_sorted(uint32_t n, const uint64_t* d_keys, uint64_t m, cudaStream_t st, const tc_options* opt,
+                              tc_graph** out) {
+    if (!out) return fail(TC_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (m && !d_keys) return fail(TC_ERR_ARG, "keys are null");
+    tc_graph* g = new tc_graph();
+    tc_status s = init_graph(g, n, opt);
+    if (s == TC_OK) s = build_from_sorted_arcs(g->s, d_keys, m, st);
+    if (s == TC_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "graph build");
+    }
+    if (s != TC_OK) {
+        std::string keep = t_err;
+        destroy(g);
+        t_err = keep;
+        return s;
+    }
+    *out = g;
+    return TC_OK;
+}
+
+}  // namespace tc
+
+extern "C" {
+
 tc_status tc_graph_create_csr(uint32_t n, const uint64_t* off, const uint32_t* adj_flagged, int ptr_is_device,
                               void* stream, const tc_options* opt, tc_graph** out) {
     if (!out) return fail(TC_ERR_ARG, "out is null");

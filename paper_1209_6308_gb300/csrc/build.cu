@@ -165,16 +165,18 @@ constexpr int kLongThreads = 1024;
 // keeping running counts of the direction classes of the entries behind the block and adding,
 // per lane, the block's entries after its own by ballot: so the lane at position k knows the
 // counts of the entries after k.  At a lower neighbour u = N[v][k] (k < up[v]) those are the
-// third vertices w > u reached from v: the lane finds the upper pair (u, v) in N[u] by binary
-// search and writes rp = k and vs = (class-1, class-2 counts).  At an upper neighbour
+// third vertices w > u reached from v: the lane writes them to sfx[lb[v] + k] (lb[v] = the
+// lower entries of the vertices before v), where k_pair_rp picks them up for the upper pair
+// (u, v).  At an upper neighbour
 // (k >= up[v]) they are the third vertices w > N[v][k] reached from v, the u side of the pair
 // (v, N[v][k]): us = (class-1, class-2 counts).  wk[0] += the suffix lengths at lower
 // neighbours (the N[v] entries a census walks), wk[1] += those of them with ids below
 // kMapIdsSuffix: with c the entries of N[v] below it (a prefix), the walk past position k
 // meets max(0, c - k - 1) of them.
 __global__ void k_pair_tables(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
-                              const uint32_t* __restrict__ up, const uint64_t* __restrict__ ub, uint32_t n,
-                              uint32_t* rp, uint2* vs, uint2* us, unsigned long long* wk) {
+                              const uint32_t* __restrict__ up, const uint64_t* __restrict__ ub,
+                              const uint64_t* __restrict__ lb, uint32_t n, uint2* sfx, uint2* us,
+                              unsigned long long* wk) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t after = lane == 31 ? 0u : ~((2u << lane) - 1u);   // lanes above this one
@@ -190,15 +192,7 @@ __global__ void k_pair_tables(const uint64_t* __restrict__ off, const uint32_t* 
             const uint32_t b1 = __ballot_sync(0xffffffffu, (e & 3u) == 1u);
             const uint32_t b2 = __ballot_sync(0xffffffffu, (e & 3u) == 2u);
             if (k < lv) {
-                const uint32_t u = e >> 2;
-                uint64_t lo = off[u] + up[u], hi = off[u + 1];
-                while (lo < hi) {
-                    const uint64_t mid = (lo + hi) >> 1;
-                    if ((adj[mid] >> 2) < (uint32_t)v) lo = mid + 1; else hi = mid;
-                }
-                const uint64_t idx = ub[u] + (lo - off[u] - up[u]);
-                rp[idx] = k;
-                vs[idx] = make_uint2(c1 + __popc(b1 & after), c2 + __popc(b2 & after));
+                sfx[lb[v] + k] = make_uint2(c1 + __popc(b1 & after), c2 + __popc(b2 & after));
                 walk += dv - k - 1;
             } else if (k < dv) {
                 us[ub[v] + (k - lv)] = make_uint2(c1 + __popc(b1 & after), c2 + __popc(b2 & after));
@@ -223,7 +217,8 @@ __global__ void k_pair_tables(const uint64_t* __restrict__ off, const uint32_t* 
 // it, as k_pair_tables walks a whole list.
 __global__ void __launch_bounds__(kLongThreads) k_pair_tables_long(
         const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj, const uint32_t* __restrict__ up,
-        const uint64_t* __restrict__ ub, uint32_t n, uint32_t* rp, uint2* vs, uint2* us, unsigned long long* wk) {
+        const uint64_t* __restrict__ ub, const uint64_t* __restrict__ lb, uint32_t n, uint2* sfx, uint2* us,
+        unsigned long long* wk) {
     __shared__ uint32_t s_c1[kLongThreads / 32], s_c2[kLongThreads / 32], s_map[kLongThreads / 32];
     const uint64_t v = blockIdx.x;
     if (v >= n) return;
@@ -267,15 +262,7 @@ __global__ void __launch_bounds__(kLongThreads) k_pair_tables_long(
             const uint32_t b1 = __ballot_sync(0xffffffffu, (e & 3u) == 1u);
             const uint32_t b2 = __ballot_sync(0xffffffffu, (e & 3u) == 2u);
             if (k < lv) {
-                const uint32_t u = e >> 2;
-                uint64_t lo = off[u] + up[u], hi = off[u + 1];
-                while (lo < hi) {
-                    const uint64_t mid = (lo + hi) >> 1;
-                    if ((adj[mid] >> 2) < (uint32_t)v) lo = mid + 1; else hi = mid;
-                }
-                const uint64_t idx = ub[u] + (lo - off[u] - up[u]);
-                rp[idx] = k;
-                vs[idx] = make_uint2(c1 + __popc(b1 & after), c2 + __popc(b2 & after));
+                sfx[lb[v] + k] = make_uint2(c1 + __popc(b1 & after), c2 + __popc(b2 & after));
                 walk += dv - k - 1;
             } else if (k < s1) {
                 us[ub[v] + (k - lv)] = make_uint2(c1 + __popc(b1 & after), c2 + __popc(b2 & after));
@@ -291,6 +278,52 @@ __global__ void __launch_bounds__(kLongThreads) k_pair_tables_long(
         const unsigned long long m = min(lv, cmap);
         const unsigned long long wm = m * cmap - m * (m + 1) / 2;
         if (wm) atomicAdd(wk + 1, wm);
+    }
+}
+
+// Position of u in the lower part L = N[v][0, len) of a list (u is there: u < v and u ~ v).
+// The degree order puts u, of degree at least v's, near the front of L, so the search gallops
+// from the front (probes 1, 3, 7, ...) and then bisects the last gap: a hub's position costs a
+// probe or two in the first sector of L.
+__device__ __forceinline__ uint32_t lower_position(const uint32_t* __restrict__ L, uint32_t len, uint32_t u) {
+    uint32_t lo = 0, hi = 1;
+    while (hi < len && (L[hi] >> 2) < u) {
+        lo = hi + 1;
+        hi = 2 * hi + 1;
+    }
+    hi = min(hi, len);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((L[mid] >> 2) < u) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// rp and vs of the upper pairs of u: for pair (u, v = N[u][j]), rp = the position k of u in
+// N[v] and vs = sfx[lb[v] + k] (the class counts of N[v] past u, from k_pair_tables).  Entries
+// j of each upper list in order, so the table writes are coalesced.  The upper pairs of one
+// vertex u go to one warp (lists of at most kLongList entries) or, for longer lists, to one
+// CTA (rp_long; those vertices are a prefix of the ids).
+template <bool LONG>
+__global__ void k_pair_rp(const uint64_t* __restrict__ off, const uint32_t* __restrict__ adj,
+                          const uint32_t* __restrict__ up, const uint64_t* __restrict__ ub,
+                          const uint64_t* __restrict__ lb, const uint2* __restrict__ sfx, uint32_t n, uint32_t* rp,
+                          uint2* vs) {
+    const uint32_t lanes = LONG ? blockDim.x : 32u;
+    const uint32_t lane = LONG ? threadIdx.x : (threadIdx.x & 31u);
+    const uint64_t stride = LONG ? gridDim.x : ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t u = LONG ? blockIdx.x : (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += stride) {
+        const uint64_t ob = off[u];
+        const uint32_t du = (uint32_t)(off[u + 1] - ob), upu = up[u];
+        if ((du > kLongList) != LONG) continue;      // uniform over the warp / CTA
+        const uint64_t tb = ub[u];
+        for (uint32_t j = upu + lane; j < du; j += lanes) {
+            const uint32_t v = adj[ob + j] >> 2;
+            const uint32_t k = lower_position(adj + off[v], up[v], (uint32_t)u);
+            rp[tb + (j - upu)] = k;
+            vs[tb + (j - upu)] = sfx[lb[v] + k];
+        }
     }
 }
 
@@ -355,11 +388,6 @@ __global__ void k_upper_counts(const uint64_t* off, const uint32_t* adj, uint32_
     }
 }
 
-int bits_for(uint32_t n) {
-    int B = 1;
-    while ((1ull << B) < n) ++B;
-    return B;
-}
 
 // Steps shared by both inputs: E unique pairs (ukey = lo<<B | hi, udir relative to lo) and
 // degrees -> relabel, CSR, up[], stats.
@@ -424,18 +452,30 @@ tc_status finish_graph(GraphStore& g, uint64_t E, int B, uint64_t* ukey, uint32_
         }
         TC_TRY(scan_u32_to_u64(ucnt.as<uint32_t>(), g.ub.as<uint64_t>(), n, st));
         if (E) {
+            // lower entries before each vertex (lb[n] = E), and their suffix counts
+            DevBuf lb, sfx;
+            TC_TRY(lb.alloc(sizeof(uint64_t) * (n + 1ull), st));
+            TC_TRY(sfx.alloc(sizeof(uint2) * E, st));
+            TC_TRY(scan_u32_to_u64(g.up.as<uint32_t>(), lb.as<uint64_t>(), n, st));
             // the walk lengths go to stats[8..9]
             k_pair_tables<<<grid_for((uint64_t)n * 32, kB, 1u << 16), kB, 0, st>>>(
-                g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(),
-                                                g.ub.as<uint64_t>(), n, g.rp.as<uint32_t>(), g.vs.as<uint2>(), g.us.as<uint2>(),
-                                                stats.as<unsigned long long>() + 8);
+                g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(), g.ub.as<uint64_t>(),
+                lb.as<uint64_t>(), n, sfx.as<uint2>(), g.us.as<uint2>(), stats.as<unsigned long long>() + 8);
             TC_LAUNCH("k_pair_tables");
             // lists longer than kLongList: at most 2E / kLongList of them, the first ids
             const uint64_t n_long = std::min<uint64_t>(n, 2ull * E / kLongList + 1);
             k_pair_tables_long<<<(unsigned)n_long, kLongThreads, 0, st>>>(
-                g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(), g.ub.as<uint64_t>(), n,
-                g.rp.as<uint32_t>(), g.vs.as<uint2>(), g.us.as<uint2>(), stats.as<unsigned long long>() + 8);
+                g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(), g.ub.as<uint64_t>(),
+                lb.as<uint64_t>(), n, sfx.as<uint2>(), g.us.as<uint2>(), stats.as<unsigned long long>() + 8);
             TC_LAUNCH("k_pair_tables_long");
+            k_pair_rp<false><<<grid_for((uint64_t)n * 32, kB, 1u << 16), kB, 0, st>>>(
+                g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(), g.ub.as<uint64_t>(),
+                lb.as<uint64_t>(), sfx.as<uint2>(), n, g.rp.as<uint32_t>(), g.vs.as<uint2>());
+            TC_LAUNCH("k_pair_rp");
+            k_pair_rp<true><<<(unsigned)n_long, kLongThreads, 0, st>>>(
+                g.off.as<uint64_t>(), g.adj.as<uint32_t>(), g.up.as<uint32_t>(), g.ub.as<uint64_t>(),
+                lb.as<uint64_t>(), sfx.as<uint2>(), n, g.rp.as<uint32_t>(), g.vs.as<uint2>());
+            TC_LAUNCH("k_pair_rp_long");
         }
     }
     unsigned long long hs[11];
@@ -454,6 +494,56 @@ tc_status finish_graph(GraphStore& g, uint64_t E, int B, uint64_t* ukey, uint32_
     // degrees descend with the new id, so the vertices with deg > 0 are [0, n_active)
     g.n_active = (uint32_t)hs[7];
     return TC_OK;
+}
+
+}  // namespace
+
+int bits_for(uint32_t n) {
+    int B = 1;
+    while ((1ull << B) < n) ++B;
+    return B;
+}
+
+namespace {
+
+// Runs of one pair among mv keys sorted by pair (direction bits in bits 0..1, runs adjacent)
+// -> E unique pairs (ukey = lo<<B | hi) with the OR of their direction bits.
+tc_status pairs_from_sorted(const uint64_t* kp, uint64_t mv, DevBuf& ukey, DevBuf& udir, uint32_t& E, cudaStream_t st) {
+    DevBuf flag, pos, total;
+    TC_TRY(flag.alloc(sizeof(uint32_t) * (mv ? mv : 1), st));
+    TC_TRY(pos.alloc(sizeof(uint32_t) * (mv ? mv : 1), st));
+    TC_TRY(total.alloc(sizeof(uint32_t), st));
+    E = 0;
+    if (mv) {
+        k_head_flags<<<grid_for(mv, kB, 1u << 16), kB, 0, st>>>(kp, mv, flag.as<uint32_t>());
+        TC_LAUNCH("k_head_flags");
+        TC_TRY(scan_u32(flag.as<uint32_t>(), pos.as<uint32_t>(), mv, total.as<uint32_t>(), st));
+        TC_CUDA(cudaMemcpyAsync(&E, total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        TC_CUDA(cudaStreamSynchronize(st));
+    }
+    TC_TRY(ukey.alloc(sizeof(uint64_t) * (E ? E : 1), st));
+    TC_TRY(udir.alloc(sizeof(uint32_t) * (E ? E : 1), st));
+    TC_CUDA(cudaMemsetAsync(udir.p, 0, sizeof(uint32_t) * (E ? E : 1), st));
+    if (mv) {
+        k_unique<<<grid_for(mv, kB, 1u << 16), kB, 0, st>>>(kp, mv, flag.as<uint32_t>(), pos.as<uint32_t>(),
+                                                             ukey.as<uint64_t>(), udir.as<uint32_t>());
+        TC_LAUNCH("k_unique");
+    }
+    return TC_OK;
+}
+
+// Degrees of the E unique pairs, then the relabelled CSR and its tables.
+tc_status graph_from_pairs(GraphStore& g, int B, uint32_t E, DevBuf& ukey, DevBuf& udir, DevBuf& stats,
+                           cudaStream_t st) {
+    DevBuf deg;
+    TC_TRY(deg.alloc(sizeof(uint32_t) * (g.n ? g.n : 1), st));
+    TC_CUDA(cudaMemsetAsync(deg.p, 0, sizeof(uint32_t) * (g.n ? g.n : 1), st));
+    if (E) {
+        k_degrees<<<grid_for(E, kB, 1u << 16), kB, 0, st>>>(ukey.as<uint64_t>(), udir.as<uint32_t>(), E, B,
+                                                             deg.as<uint32_t>(), stats.as<unsigned long long>());
+        TC_LAUNCH("k_degrees");
+    }
+    return finish_graph(g, E, B, ukey.as<uint64_t>(), udir.as<uint32_t>(), deg.as<uint32_t>(), stats, st);
 }
 
 }  // namespace
@@ -480,40 +570,27 @@ tc_status build_from_arcs(GraphStore& g, uint64_t m, const uint32_t* d_src, cons
     uint64_t* kp = keys.as<uint64_t>();
     uint64_t* tp = tmp.as<uint64_t>();
     TC_TRY(radix_sort_u64(&kp, &tp, m, 2, 2 * B + 2, st));
-    // unique pairs
-    DevBuf flag, pos, ukey, udir, deg, total;
-    TC_TRY(flag.alloc(sizeof(uint32_t) * (mv ? mv : 1), st));
-    TC_TRY(pos.alloc(sizeof(uint32_t) * (mv ? mv : 1), st));
-    TC_TRY(total.alloc(sizeof(uint32_t), st));
+    // unique pairs (the self-loops' all-ones keys sort past the mv valid ones)
+    DevBuf ukey, udir;
     uint32_t E = 0;
-    if (mv) {
-        k_head_flags<<<grid_for(mv, kB, 1u << 16), kB, 0, st>>>(kp, mv, flag.as<uint32_t>());
-        TC_LAUNCH("k_head_flags");
-        TC_TRY(scan_u32(flag.as<uint32_t>(), pos.as<uint32_t>(), mv, total.as<uint32_t>(), st));
-        TC_CUDA(cudaMemcpyAsync(&E, total.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        TC_CUDA(cudaStreamSynchronize(st));
-    }
-    TC_TRY(ukey.alloc(sizeof(uint64_t) * (E ? E : 1), st));
-    TC_TRY(udir.alloc(sizeof(uint32_t) * (E ? E : 1), st));
-    TC_CUDA(cudaMemsetAsync(udir.p, 0, sizeof(uint32_t) * (E ? E : 1), st));
-    if (mv) {
-        k_unique<<<grid_for(mv, kB, 1u << 16), kB, 0, st>>>(kp, mv, flag.as<uint32_t>(), pos.as<uint32_t>(),
-                                                             ukey.as<uint64_t>(), udir.as<uint32_t>());
-        TC_LAUNCH("k_unique");
-    }
+    TC_TRY(pairs_from_sorted(kp, mv, ukey, udir, E, st));
     keys.release();
     tmp.release();
-    flag.release();
-    pos.release();
-    TC_TRY(deg.alloc(sizeof(uint32_t) * n, st));
-    TC_CUDA(cudaMemsetAsync(deg.p, 0, sizeof(uint32_t) * n, st));
-    if (E) {
-        k_degrees<<<grid_for(E, kB, 1u << 16), kB, 0, st>>>(ukey.as<uint64_t>(), udir.as<uint32_t>(), E, B,
-                                                             deg.as<uint32_t>(), stats.as<unsigned long long>());
-        TC_LAUNCH("k_degrees");
-    }
-    TC_TRY(finish_graph(g, E, B, ukey.as<uint64_t>(), udir.as<uint32_t>(), deg.as<uint32_t>(), stats, st));
+    TC_TRY(graph_from_pairs(g, B, E, ukey, udir, stats, st));
     g.dups = m - g.loops - g.arcs;
+    return TC_OK;
+}
+
+tc_status build_from_sorted_arcs(GraphStore& g, const uint64_t* d_keys, uint64_t m, cudaStream_t st) {
+    const int B = bits_for(g.n);
+    if (m >= (1ull << 32)) return fail(TC_ERR_RANGE, "more than 2^32-1 arcs");
+    DevBuf stats, ukey, udir;
+    TC_TRY(stats.alloc(sizeof(unsigned long long) * 11, st));
+    TC_CUDA(cudaMemsetAsync(stats.p, 0, sizeof(unsigned long long) * 11, st));
+    uint32_t E = 0;
+    TC_TRY(pairs_from_sorted(d_keys, m, ukey, udir, E, st));
+    TC_TRY(graph_from_pairs(g, B, E, ukey, udir, stats, st));
+    g.dups = m - g.arcs;
     return TC_OK;
 }
 

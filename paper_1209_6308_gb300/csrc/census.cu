@@ -1230,7 +1230,7 @@ tc_status census_enqueue_range(GraphStore& g, const Opts& o, const Item* items, 
                                unsigned long long* d_vcost, unsigned long long* d_phase) {
     if (g.e_sym == 0) return TC_OK;
     if (o.algo == TC_ALGO_TRIANGLE)
-        return triangle_census_enqueue(g, o, items, n_items, warp_begin, warp_end, st, d_out16, d_vcost);
+        return triangle_census_enqueue(g, o, items, n_items, warp_begin, warp_end, st, d_out16, d_vcost, d_phase);
     const bool vt = g.vs.p != nullptr;
     const bool map = census_map(g, o);
     const size_t smem = census_smem(o.algo, o.chunk, map);

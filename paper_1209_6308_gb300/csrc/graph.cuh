@@ -112,6 +112,15 @@ constexpr uint32_t kMaxWave = 32;
 
 tc_status build_from_arcs(GraphStore& g, uint64_t m, const uint32_t* d_src, const uint32_t* d_dst, cudaStream_t st);
 tc_status build_from_csr(GraphStore& g, const uint64_t* d_off, const uint32_t* d_adj, cudaStream_t st);
+// From m distinct arc keys sorted ascending, each (lo << (B+2)) | (hi << 2) | dir with lo < hi the
+// pair's ids, B = bits_for(n) and dir 1 for lo -> hi, 2 for hi -> lo (a mutual pair has both).
+tc_status build_from_sorted_arcs(GraphStore& g, const uint64_t* d_keys, uint64_t m, cudaStream_t st);
+// Bits of a vertex id in the build's keys: the least B >= 1 with 2^B >= n.
+int bits_for(uint32_t n);
+// A graph (as tc_graph_create_arcs makes it, options `opt`) from m sorted distinct arc keys on
+// the device, as build_from_sorted_arcs takes them; synchronises `st`.
+tc_status graph_create_sorted(uint32_t n, const uint64_t* d_keys, uint64_t m, cudaStream_t st, const tc_options* opt,
+                              tc_graph** out);
 
 // Enqueue one census on `st`; counts of classes 1..15 are added to d_out16 (which the
 // caller zeroes; index 0 is never touched).  No host synchronisation, no allocation once
@@ -134,7 +143,7 @@ tc_status census_enqueue_range(GraphStore& g, const Opts& o, const Item* items, 
 // the given items and warp-tier range, and the fold into d_out16[1..15].
 tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items,
                                   uint32_t warp_begin, uint32_t warp_end, cudaStream_t st, unsigned long long* d_out16,
-                                  unsigned long long* d_vcost);
+                                  unsigned long long* d_vcost, unsigned long long* d_phase = nullptr);
 // Batched triangle form: k graphs (d_graphs), items tagged with the graph (pad), warp-tier
 // blocks (u0, u1, graph); d_scratch holds 96 uint64 per graph (zeroed here), graph g's counts of
 // classes 1..15 are added to d_out[16 g ..] (caller-zeroed); ctr: 4 zeroed uint32.
@@ -153,7 +162,8 @@ tc_status triangle_collect(unsigned long long* const* scratch, uint32_t n, unsig
 // tricode per rank pattern) of every triangle, added into d_hist64; ctr: 4 zeroed uint32.
 tc_status triangles_launch(const GraphDev& gd, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
                            uint32_t warp_end, uint32_t* ctr, const uint32_t* old, const uint8_t* d_perm_state,
-                           unsigned long long* d_hist64, unsigned long long* d_vcost, cudaStream_t st);
+                           unsigned long long* d_hist64, unsigned long long* d_vcost, cudaStream_t st,
+                           unsigned long long* d_phase = nullptr);
 // Cut p's work into `world` contiguous shards of about equal work (cached in p for that world);
 // synchronises st when it computes them.
 tc_status plan_shards(GraphStore& g, const Opts& o, Plan& p, uint32_t world, cudaStream_t st);

@@ -135,11 +135,17 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* key
     for (int d = threadIdx.x; d < (kSortThreads / 32) * 256; d += kSortThreads) (&wh[0][0])[d] = 0;
     __syncthreads();
     uint64_t base = (uint64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
+    // all of the thread's keys are loaded before any is counted, so the tile's loads are in
+    // flight together
+    uint32_t dg[kSortRounds];
+#pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
         uint64_t i = base + (uint64_t)r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&wh[warp][(keys[i] >> shift) & 255u], 1u);
+        dg[r] = i < n ? (uint32_t)(keys[i] >> shift) & 255u : 256u;
     }
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r)
+        if (dg[r] < 256u) atomicAdd(&wh[warp][dg[r]], 1u);
     __syncthreads();
     uint32_t s = 0;
 #pragma unroll
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* key
     counts[(uint64_t)threadIdx.x * tiles + blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* in, uint64_t* out, uint64_t n, int shift,
+__global__ void __launch_bounds__(kSortThreads, 3) k_radix_scatter(const uint64_t* in, uint64_t* out, uint64_t n, int shift,
                                                                 const uint32_t* counts, const uint32_t* offs,
                                                                 uint32_t tiles) {
     __shared__ uint64_t s_keys[kSortTile];
@@ -164,10 +170,18 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* 
     s_run[tid] = 0;
     __syncthreads();
 
+    // the thread's keys of all rounds, loaded together (coalesced, one tile in flight)
+    uint64_t kr[kSortRounds];
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        uint64_t i = base + (uint64_t)r * kSortThreads + tid;
+        kr[r] = i < n ? in[i] : 0ull;
+    }
+#pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
         uint64_t i = base + (uint64_t)r * kSortThreads + tid;
         bool valid = i < n;
-        uint64_t k = valid ? in[i] : 0ull;
+        uint64_t k = kr[r];
         uint32_t d = (uint32_t)(k >> shift) & 255u;
 #pragma unroll
         for (int q = 0; q < 8; ++q) s_wc[warp][lane + 32 * q] = 0;

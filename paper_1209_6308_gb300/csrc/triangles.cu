@@ -41,6 +41,12 @@ constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kWarpSlots = 256;     // per-warp hash slots: |L(b)| <= warp_max_deg <= 128
 constexpr uint32_t kFlushElems = 1u << 30;
 
+__device__ __forceinline__ unsigned long long tri_clock_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 __device__ __forceinline__ uint32_t tri_hash(uint32_t x, int hb) { return (x * 2654435761u) >> (32 - hb); }
 
 // tricode of the triangle (a, b, c) from three stored entries: e_ba = a in N[b] (bits seen from
@@ -63,6 +69,7 @@ struct TriParams {
     unsigned long long* hist;     // 64 bins (triangle tricodes, or states with OLD); batched: graph g's at
                                   // hist + kBatchStride g
     unsigned long long* vcost;    // optional [n]: SM cycles per CTA-tier vertex b
+    unsigned long long* phase;    // optional [3 * gridDim]: globaltimer at start, end of items, end
     // batched launch: item.pad is the graph index, warp-tier blocks are (u0, u1, graph)
     const GraphDev* graphs;
     const uint4* wblocks;
@@ -231,6 +238,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
     __shared__ uint32_t s_item, s_next;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (P.phase && tid == 0) P.phase[3 * blockIdx.x] = tri_clock_ns();
     for (int k = tid; k < kWarps * 64; k += kThreads) sHist[k] = 0u;
     if (OLD)
         for (int k = tid; k < 9 * 64; k += kThreads) sPerm[k] = P.perm_state[k];
@@ -332,6 +340,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
         __syncthreads();   // every thread has read s_item before thread 0 takes the next item
     }
 
+    if (P.phase && tid == 0) P.phase[3 * blockIdx.x + 1] = tri_clock_ns();
+
     // ---------------------------------------------------------------- one warp per vertex
     uint32_t* wH = sWH + warp * kWarpSlots;
     uint32_t* wO = sWO + (OLD ? warp * kWarpSlots : 0u);
@@ -390,6 +400,10 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
         }
     }
     if (MODE == kTriSingle || cur_graph != 0xffffffffu) flush_warp_hist(myHist, ghist, lane);
+    if (P.phase) {   // uniform over the CTA
+        __syncthreads();
+        if (tid == 0) P.phase[3 * blockIdx.x + 2] = tri_clock_ns();
+    }
 }
 
 // One pair's bulk sums into acc (see k_pair_bulk): u of degree du, the pair's entry e = N[u][j]
@@ -686,7 +700,8 @@ tc_status fold_table(Table64* T) {
 
 tc_status triangles_launch(const GraphDev& gd, const Opts& o, const Item* items, uint32_t n_items, uint32_t warp_begin,
                            uint32_t warp_end, uint32_t* ctr, const uint32_t* old, const uint8_t* d_perm_state,
-                           unsigned long long* d_hist64, unsigned long long* d_vcost, cudaStream_t st) {
+                           unsigned long long* d_hist64, unsigned long long* d_vcost, cudaStream_t st,
+                           unsigned long long* d_phase) {
     const bool is_old = old != nullptr;
     const size_t smem = tri_smem(o.chunk, is_old);
     TC_TRY(tri_prepare(is_old ? 1 : 0, smem));
@@ -704,6 +719,7 @@ tc_status triangles_launch(const GraphDev& gd, const Opts& o, const Item* items,
     P.perm_state = d_perm_state;
     P.hist = d_hist64;
     P.vcost = d_vcost;
+    P.phase = d_phase;
     const unsigned grid = (unsigned)census_grid(o);
     if (is_old) k_triangles<true, kTriSingle><<<grid, kThreads, smem, st>>>(P);
     else k_triangles<false, kTriSingle><<<grid, kThreads, smem, st>>>(P);
@@ -713,7 +729,7 @@ tc_status triangles_launch(const GraphDev& gd, const Opts& o, const Item* items,
 
 tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* items, uint32_t n_items,
                                   uint32_t warp_begin, uint32_t warp_end, cudaStream_t st, unsigned long long* d_out16,
-                                  unsigned long long* d_vcost) {
+                                  unsigned long long* d_vcost, unsigned long long* d_phase) {
     if (g.e_sym == 0) return TC_OK;
     if (!g.vs.p) return fail(TC_ERR_ARG, "the triangle form needs the per upper pair tables");
     if (!g.tri.p) TC_TRY(g.tri.alloc_persistent(sizeof(unsigned long long) * kBatchStride));
@@ -737,7 +753,7 @@ tc_status triangle_census_enqueue(GraphStore& g, const Opts& o, const Item* item
         TC_LAUNCH("k_pair_bulk");
     }
     TC_TRY(triangles_launch(gd, o, items, n_items, warp_begin, warp_end, g.ctr.as<uint32_t>(), nullptr, nullptr, hist,
-                            d_vcost, st));
+                            d_vcost, st, d_phase));
     Table64 T;
     TC_TRY(fold_table(&T));
     k_tri_fold<<<1, 64, 0, st>>>(raw, hist, T, d_out16);

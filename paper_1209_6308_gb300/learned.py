@@ -18,7 +18,8 @@ import time
 
 import numpy as np
 
-from . import (TC_ALGO_SUFFIX, TC_SCHED_LEARNED, Graph, tc_census_async, tc_census_profile, tc_costmodel_create,
+from . import (TC_ALGO_SUFFIX, TC_SCHED_LEARNED, Graph, tc_census_async, tc_census_grid, tc_census_profile,
+               tc_costmodel_create,
                tc_costmodel_fit_norm, tc_costmodel_predict, tc_costmodel_samples, tc_costmodel_train,
                tc_graph_attach_costmodel, tc_graph_features)
 
@@ -125,6 +126,27 @@ def census_ms(g: Graph, options, stream_obj, reps: int = 5):
         stream_obj.synchronize()
         ts.append(e0.elapsed_time(e1))
     return statistics.median(ts), [int(x) & ((1 << 64) - 1) for x in out.cpu().tolist()]
+
+
+def balance(g: Graph, options, stream=None, reps: int = 3):
+    """Work balance of the census under `options` from its per-CTA timestamps (the last of `reps`
+    profiled runs; in the triangle form, of the triangle walk): the makespan, the mean CTA busy
+    time as a fraction of it, and the tail (the last CTA's end less the median CTA's end)."""
+    import torch
+    grid = tc_census_grid(options)
+    out = torch.zeros(16, dtype=torch.int64, device="cuda")
+    vcost = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+    phase = torch.zeros(3 * grid, dtype=torch.int64, device="cuda")
+    for _ in range(reps):
+        vcost.zero_()
+        tc_census_profile(g.handle, out, vcost, phase, stream=stream, options=options)
+    torch.cuda.synchronize()
+    ph = phase.view(-1, 3).cpu().numpy().astype(np.int64)
+    start, end = ph[:, 0], ph[:, 2]
+    makespan = float(end.max() - start.min())
+    return {"ctas": grid, "makespan_ms": makespan * 1e-6,
+            "mean_busy_frac": float((end - start).mean()) / makespan if makespan > 0 else 1.0,
+            "tail_ms": float(end.max() - np.median(end)) * 1e-6}
 
 
 def attach(model, g: Graph, stream=None):

@@ -91,3 +91,70 @@ def test_empty_window_and_time_order_errors(tc):
         with pytest.raises(tc.TcError) as e:
             st.push([1], [2], [8])                            # arc times must not decrease
         assert e.value.status == tc.TC_ERR_ARG
+
+
+def _distinct(src, dst, sel):
+    """Distinct non-loop arcs among the selected ones."""
+    s, d = src[sel].astype(np.int64), dst[sel].astype(np.int64)
+    keep = s != d
+    return len(np.unique(s[keep] * (1 << 32) + d[keep]))
+
+
+def test_arc_set_is_updated_incrementally(tc):
+    """Small steps: after the first census every window is reached by merging the arcs that
+    entered and left into the kept set (no rebuild, no repair), the set holds exactly the
+    window's distinct arcs, and every census equals the oracle's."""
+    n, src, dst, t = _timeline(7)
+    window = 300
+    with tc.Stream(n, window, options={"algo": 2}) as st:
+        st.push(src, dst, t)
+        prev_a, prev_b = 0, 0
+        for k, t_now in enumerate(range(100, 1000, 37)):
+            got, m = st.census(t_now)
+            want, wm = _want(n, src, dst, t, t_now, window)
+            assert (got, m) == (want, wm), t_now
+            sel = (t <= t_now) & ((t > t_now - window) if t_now >= window else True)
+            a = int(np.searchsorted(t, t_now - window, side="right")) if t_now >= window else 0
+            b = int(np.searchsorted(t, t_now, side="right"))
+            info = st.stats()
+            assert info["distinct_arcs"] == _distinct(src, dst, sel)
+            assert info["repairs"] == 0
+            if k == 0:
+                assert info["rebuilds"] == 1 and info["last_added"] == b
+            else:
+                assert info["rebuilds"] == 1, t_now                  # merged, not rebuilt
+                assert info["last_added"] == b - prev_b and info["last_evicted"] == a - prev_a
+            prev_a, prev_b = a, b
+
+
+def test_a_jump_past_the_window_rebuilds_the_set(tc):
+    n, src, dst, t = _timeline(8)
+    window = 100
+    with tc.Stream(n, window) as st:
+        st.push(src, dst, t)
+        for t_now, rebuilt in ((150, 1), (180, 1), (600, 2), (610, 2), (999, 3)):
+            got, m = st.census(t_now)
+            assert (got, m) == _want(n, src, dst, t, t_now, window)
+            info = st.stats()
+            assert (info["rebuilds"], info["repairs"]) == (rebuilt, 0), t_now
+
+
+def test_a_repeated_arc_stays_until_its_last_copy_leaves(tc):
+    n = 10
+    c3 = n * (n - 1) * (n - 2) // 6
+    one_arc = [c3 - (n - 2), n - 2] + [0] * 14          # one arc: n - 2 triads 012, the rest 003
+    empty = [c3] + [0] * 15
+    with tc.Stream(n, 5) as st:
+        st.push([1, 1, 4], [2, 2, 4], [1, 5, 6])         # 1 -> 2 twice, and a self-loop
+        assert st.census(5) == (one_arc, 2)
+        assert st.stats()["distinct_arcs"] == 1
+        assert st.census(7) == (one_arc, 2)              # the copy at time 1 left, the one at 5 stays
+        assert st.stats()["distinct_arcs"] == 1
+        assert st.census(9) == (one_arc, 2)
+        assert st.census(10) == (empty, 1)               # (5, 10]: only the self-loop is left
+        info = st.stats()
+        assert info["distinct_arcs"] == 0 and info["repairs"] == 0
+        st.push([2], [1], [12])                          # the reverse arc: 102 if both were in
+        assert st.census(12) == (one_arc, 1)
+        assert st.census(16) == (one_arc, 1)
+        assert st.stats()["repairs"] == 0
