@@ -763,7 +763,7 @@ def run_gpu(args):
     log(f"timed: {ms:.2f} ms per step")
 
     # end to end through the C ABI from pinned host buffers
-    e2e_ms, e2e_counts = [], None
+    e2e_ms, e2e_build_ms, e2e_counts = [], [], None
     if args.e2e_steps > 0:
         src_pin = torch.from_numpy(s.view("int32")).pin_memory()
         dst_pin = torch.from_numpy(d.view("int32")).pin_memory()
@@ -774,6 +774,7 @@ def run_gpu(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = tc.tc_graph_create_arcs(n, src_pin, dst_pin, stream=sh, options=opts)
+            t_built = time.perf_counter()
             if world == 1:
                 c = tc.tc_census(h, stream=sh, options=opts)
             else:
@@ -783,6 +784,7 @@ def run_gpu(args):
             tc.tc_graph_destroy(h)
             if i:
                 e2e_ms.append(dt)
+                e2e_build_ms.append((t_built - t0) * 1e3)
             e2e_counts = c
         del src_pin, dst_pin
     e2e_job_ms = max_over_ranks(dist, statistics.mean(e2e_ms), "cuda") if e2e_ms else None
@@ -869,7 +871,10 @@ def run_gpu(args):
         "roofline": roof,
         "e2e": ({"value": job_value(arcs, e2e_job_ms), "unit": "arcs/s",
                  "h2d_bytes_per_step": 8 * arcs, "d2h_bytes_per_step": 16 * 16,
-                 "ms_per_step": e2e_job_ms} if e2e_ms else None),
+                 "ms_per_step": e2e_job_ms,
+                 "build_ms": statistics.mean(e2e_build_ms) if e2e_build_ms else None,
+                 "path": "tc_graph_create_arcs from page-locked host arcs (read by the build's key kernel over "
+                         "the host link), tc_census (plan + census), 16 counts to the host"} if e2e_ms else None),
         # per census: k_pair_bulk, k_triangles, k_tri_fold (triangle form) or k_census
         "gpu_launches": args.steps * (3 if algo == tc.TC_ALGO_TRIANGLE else 1),
         "clocks": clk.summary(),

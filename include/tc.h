@@ -118,7 +118,9 @@ typedef struct {
 
 /* Build a graph from an arc list (Sec. 6, Fig. 7).  src[i] -> dst[i] for i < m; self-loops
  * and repeated arcs are dropped and counted.  Ids >= n give TC_ERR_RANGE.  src/dst are
- * device pointers if ptr_is_device, else host pointers (copied to the device on `stream`).
+ * device pointers if ptr_is_device, else host pointers: page-locked host arrays (cudaHostAlloc,
+ * cudaHostRegister) are read once by the build's first kernel directly over the host link,
+ * pageable ones are copied to the device on `stream` first.
  * Vertices are relabelled by descending symmetric degree (ties by original id); the census
  * does not depend on labels.  opt may be NULL.  The call synchronises `stream`. */
 tc_status tc_graph_create_arcs(uint32_t n, uint64_t m, const uint32_t* src, const uint32_t* dst,

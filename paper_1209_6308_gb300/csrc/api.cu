@@ -201,6 +201,18 @@ tc_status upload(const T* h, uint64_t count, DevBuf& b, cudaStream_t st) {
     return TC_OK;
 }
 
+// The device's address of page-locked host memory (cudaHostAlloc / cudaHostRegister), which a
+// kernel can read directly over the host link, or null for any other pointer.
+template <typename T>
+const T* mapped_host(const T* h) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer ? static_cast<const T*>(a.devicePointer) : nullptr;
+}
+
 }  // namespace
 }  // namespace tc
 
@@ -241,6 +253,17 @@ tc_status tc_graph_create_arcs(uint32_t n, uint64_t m, const uint32_t* src, cons
     if (s == TC_OK) {
         if (ptr_is_device) {
             s = build_from_arcs(g->s, m, src, dst, st);
+        } else if (const uint32_t* ms = m ? mapped_host(src) : nullptr) {
+            // page-locked arcs: the key kernel, which reads each arc once, reads them over the
+            // host link, so there is no device copy to write and read back
+            const uint32_t* md = mapped_host(dst);
+            if (md) {
+                s = build_from_arcs(g->s, m, ms, md, st);
+            } else {
+                DevBuf dd;
+                s = upload(dst, m, dd, st);
+                if (s == TC_OK) s = build_from_arcs(g->s, m, ms, dd.as<uint32_t>(), st);
+            }
         } else {
             DevBuf ds, dd;
             s = upload(src, m, ds, st);

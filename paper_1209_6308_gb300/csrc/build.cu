@@ -62,16 +62,26 @@ __global__ void k_unique(const uint64_t* keys, uint64_t cnt, const uint32_t* fla
     }
 }
 
-// degrees; stats[2] mutual pairs
+// degrees; stats[2] mutual pairs.  The pairs are sorted by their smaller id, so the lanes of a
+// warp mostly share it: one atomic per run of equal ids (a hub's run would otherwise serialise
+// thousands of atomics on one address).
 __global__ void k_degrees(const uint64_t* ukey, const uint32_t* udir, uint64_t E, int B, uint32_t* deg,
                           unsigned long long* stats) {
     const uint64_t mask = (1ull << B) - 1;
+    const uint32_t lane = threadIdx.x & 31;
     uint32_t mut = 0;
-    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < E; r += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t k = ukey[r];
-        atomicAdd(&deg[k >> B], 1u);
-        atomicAdd(&deg[k & mask], 1u);
-        mut += (udir[r] == 3u);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t r0 = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); r0 < E; r0 += stride) {
+        const uint64_t r = r0 + lane;   // uniform loop over the warp: every lane takes part in the match
+        const bool ok = r < E;
+        const uint64_t k = ok ? ukey[r] : ~0ull;
+        const uint32_t lo = (uint32_t)(k >> B);
+        const uint32_t peers = __match_any_sync(0xffffffffu, ok ? lo : 0xffffffffu);
+        if (ok && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&deg[lo], (uint32_t)__popc(peers));
+        if (ok) {
+            atomicAdd(&deg[k & mask], 1u);
+            mut += (udir[r] == 3u);
+        }
     }
     for (int o = 16; o; o >>= 1) mut += __shfl_xor_sync(0xffffffffu, mut, o);
     if ((threadIdx.x & 31) == 0 && mut) atomicAdd(&stats[2], (unsigned long long)mut);
@@ -312,7 +322,8 @@ __global__ void k_pair_rp(const uint64_t* __restrict__ off, const uint32_t* __re
                           uint2* vs) {
     const uint32_t lanes = LONG ? blockDim.x : 32u;
     const uint32_t lane = LONG ? threadIdx.x : (threadIdx.x & 31u);
-    const uint64_t stride = LONG ? gridDim.x : ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    // LONG: one CTA per vertex of the prefix the grid covers (the long lists are among them)
+    const uint64_t stride = LONG ? n : ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t u = LONG ? blockIdx.x : (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += stride) {
         const uint64_t ob = off[u];
         const uint32_t du = (uint32_t)(off[u + 1] - ob), upu = up[u];

@@ -337,3 +337,25 @@ def test_rmat_scale20_hub_core_matches_oracle(tc, rmat20):
     for opts in ({"algo": 0}, {"algo": 1}, {"algo": 1, "chunk_entries": 512, "warp_max_deg": 4}, {"algo": 2},
                  {"algo": 2, "chunk_entries": 512, "warp_max_deg": 4}):
         assert gpu_census(tc, k, ss, dd, opts) == want
+
+
+def test_page_locked_host_arcs_are_read_in_place(tc):
+    """Arcs in page-locked host memory (read by the build's key kernel over the host link), in
+    pageable host memory (copied first) and on the device give the same graph and census."""
+    import torch
+    n, s, d = graphgen.rmat(12, 16, 0.2, 21)
+    s = np.concatenate([s, s[:100], np.arange(50, dtype=np.uint32)])   # repeats and loops
+    d = np.concatenate([d, d[:100], np.arange(50, dtype=np.uint32)])
+    want = oracle.census_bm(n, s, d)
+    pin_s = torch.from_numpy(s.view(np.int32)).pin_memory()
+    pin_d = torch.from_numpy(d.view(np.int32)).pin_memory()
+    stats = []
+    for src, dst in ((pin_s, pin_d), (s, d), (pin_s.cuda(), pin_d.cuda())):
+        with tc.Graph(tc.tc_graph_create_arcs(n, src, dst), n) as g:
+            assert g.census() == want
+            st = g.stats()
+            stats.append((st["e_sym"], st["arcs"], st["loops_dropped"], st["dups_dropped"]))
+    assert stats[0] == stats[1] == stats[2]
+    # one page-locked array and one pageable: the pageable one is copied
+    with tc.Graph(tc.tc_graph_create_arcs(n, pin_s, d), n) as g:
+        assert g.census() == want

@@ -116,3 +116,27 @@ def test_learned_schedule_is_exact_and_predicts_cost_better(tc):
         assert q["rms_log_err_model"] < q["rms_log_err_degree"], q
     finally:
         tc.tc_costmodel_destroy(model)
+
+
+def test_learned_schedule_keeps_the_work_balance(tc):
+    """The plain schedule (items cut by exact pair work) is the fallback and the yardstick: on a
+    held-out graph the learned schedule of the triangle form must give the oracle's counts and
+    a makespan, from the per-CTA timestamps of the profiled census, no worse than the plain
+    one's beyond timing noise; both must keep the CTAs busy most of the makespan."""
+    from paper_1209_6308_gb300 import learned
+    tri = {"algo": tc.TC_ALGO_TRIANGLE}
+    model, info = learned.train_cost_model(scales=(14, 15, 16), seeds=(51, 52, 53), steps=300, options=tri)
+    try:
+        n, s, d = graphgen.rmat(17, 16, 0.2, 78)                # held-out graph
+        want = oracle.census_bm_parallel(n, s, d)
+        with tc.Graph.from_arcs(n, s, d, options=tri) as g:
+            learned.attach(model, g)
+            lrn = dict(tri, schedule=tc.TC_SCHED_LEARNED)
+            assert g.census(options=lrn) == want
+            bp = learned.balance(g, tri)
+            bl = learned.balance(g, lrn)
+        assert bl["ctas"] == bp["ctas"] > 0
+        assert bl["makespan_ms"] <= 1.25 * bp["makespan_ms"] + 0.05, (bp, bl)
+        assert bp["mean_busy_frac"] > 0.5 and bl["mean_busy_frac"] > 0.5, (bp, bl)
+    finally:
+        tc.tc_costmodel_destroy(model)
