@@ -49,11 +49,13 @@ __device__ __forceinline__ unsigned long long tri_clock_ns() {
 
 __device__ __forceinline__ uint32_t tri_hash(uint32_t x, int hb) { return (x * 2654435761u) >> (32 - hb); }
 
-// tricode of the triangle (a, b, c) from three stored entries: e_ba = a in N[b] (bits seen from
-// b: 1 b->a, 2 a->b), e_bc = c in N[b] (1 b->c, 2 c->b), e_ca = a in N[c] (1 c->a, 2 a->c).
-// Tricode bits: 1 b->a, 2 a->b, 4 b->c, 8 c->b, 16 a->c, 32 c->a.
-__device__ __forceinline__ uint32_t tri_code(uint32_t e_ba, uint32_t e_bc, uint32_t e_ca) {
-    return (e_ba & 3u) | ((e_bc & 3u) << 2) | (((e_ca >> 1) & 1u) << 4) | ((e_ca & 1u) << 5);
+// Tricode of the triangle (a, b, c) from the direction bits of three stored entries: a in N[b]
+// (seen from b: 1 b->a, 2 a->b), c in N[b] (1 b->c, 2 c->b) and a in N[c] (1 c->a, 2 a->c).
+// Tricode bits: 1 b->a, 2 a->b, 4 b->c, 8 c->b, 16 a->c, 32 c->a.  The walk keeps the second
+// term pre-shifted per pair (bc_bits = (dir(b,c)) << 2) and maps the third through a four-entry
+// byte table: dir(c,a) 1 -> 32, 2 -> 16, 3 -> 48.
+__device__ __forceinline__ uint32_t tri_code(uint32_t dir_ba, uint32_t bc_bits, uint32_t e_ca) {
+    return dir_ba | bc_bits | __byte_perm(0x30102000u, 0u, e_ca & 3u);
 }
 
 struct TriParams {
@@ -140,6 +142,10 @@ __device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, const GraphDe
         const uint32_t excl = incl - len;
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         walked += total;
+        // entry i of the flattened range lies at adj[cbx + i] for the pair that holds it (modular
+        // arithmetic: i >= excl), and its tricode's b-c bits are bcb
+        const uint64_t cbx = cb - excl;
+        const uint32_t bcb = (e_bc & 3u) << 2;
         int seg_prev = -1;
         // two rounds of 32 entries per iteration, so each lane has two loads in flight
         for (uint32_t base = 0; base < total; base += 64) {
@@ -149,43 +155,43 @@ __device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, const GraphDe
             const bool stB = (uint32_t)lane < cnt && excl >= base + 32u && excl < base + 64u;
             const uint32_t MA = __reduce_or_sync(0xffffffffu, stA ? (1u << (excl - base)) : 0u);
             const uint32_t MB = __reduce_or_sync(0xffffffffu, stB ? (1u << (excl - base - 32u)) : 0u);
+            // (lane 31's count covers the whole round: the last pair of a round needs no shuffle)
             const int segA = seg_prev + __popc(MA & le_mask);
-            const int lastA = __shfl_sync(0xffffffffu, segA, 31);
+            const int lastA = seg_prev + __popc(MA);
             const int segB = lastA + __popc(MB & le_mask);
-            seg_prev = __shfl_sync(0xffffffffu, segB, 31);
+            seg_prev = lastA + __popc(MB);
             const uint32_t sa = (uint32_t)segA & 31u, sb = (uint32_t)segB & 31u;
-            const uint32_t PA = __shfl_sync(0xffffffffu, excl, sa), PB = __shfl_sync(0xffffffffu, excl, sb);
-            const uint64_t BA = __shfl_sync(0xffffffffu, cb, sa), BB = __shfl_sync(0xffffffffu, cb, sb);
-            const uint32_t EA = __shfl_sync(0xffffffffu, e_bc, sa), EB = __shfl_sync(0xffffffffu, e_bc, sb);
+            const uint64_t BA = __shfl_sync(0xffffffffu, cbx, sa), BB = __shfl_sync(0xffffffffu, cbx, sb);
+            const uint32_t EA = __shfl_sync(0xffffffffu, bcb, sa), EB = __shfl_sync(0xffffffffu, bcb, sb);
             uint32_t OA = 0, OB = 0;
             if (OLD) {
                 OA = __shfl_sync(0xffffffffu, oc, sa);
                 OB = __shfl_sync(0xffffffffu, oc, sb);
             }
             const uint32_t iA = base + lane, iB = base + 32u + lane;
-            const uint32_t xA = iA < total ? __ldg(adj + BA + (iA - PA)) : 0u;
-            const uint32_t xB = iB < total ? __ldg(adj + BB + (iB - PB)) : 0u;
+            const uint32_t xA = iA < total ? __ldg(adj + (BA + iA)) : 0u;
+            const uint32_t xB = iB < total ? __ldg(adj + (BB + iB)) : 0u;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const uint32_t e_ca = r ? xB : xA;
                 if (!e_ca) continue;
                 const uint32_t a = e_ca >> 2;
-                uint32_t e, oa = 0;
-                if (MAP) {
-                    const uint32_t dir = (sH[a >> 4] >> ((a & 15u) << 1)) & 3u;
-                    e = dir ? ((a << 2) | dir) : 0u;
+                uint32_t dir, oa = 0;
+                if (MAP) {   // word a / 16, bits 2 (a mod 16), read straight from the entry
+                    dir = (sH[e_ca >> 6] >> ((e_ca >> 1) & 30u)) & 3u;
                     if (OLD && dir) oa = P.old[a];
                 } else {
                     uint32_t h = tri_hash(a, hb);
-                    e = sH[h];
+                    uint32_t e = sH[h];
                     while (e != 0u && (e >> 2) != a) {
                         h = (h + 1u) & hmask;
                         e = sH[h];
                     }
+                    dir = e & 3u;
                     if (OLD && e) oa = sO[h];
                 }
-                if (e != 0u) {
-                    uint32_t t = tri_code(e, r ? EB : EA, e_ca);
+                if (dir != 0u) {
+                    uint32_t t = tri_code(dir, r ? EB : EA, e_ca);
                     if (OLD) {
                         const uint32_t oc2 = r ? OB : OA;
                         const uint32_t ra = (oa > ob) + (oa > oc2), rb = (ob > oa) + (ob > oc2);
