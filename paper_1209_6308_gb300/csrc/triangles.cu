@@ -38,6 +38,11 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+// Prefixes of at least kLongPrefix entries are walked one pair at a time by the whole warp,
+// kLongRounds loads of 32 entries in flight per lane; shorter ones share flattened ranges.
+// (Swept at scales 20 and 26: thresholds 64-512, 2-8 rounds.)
+constexpr uint32_t kLongPrefix = 128;
+constexpr int kLongRounds = 8;
 constexpr uint32_t kWarpSlots = 256;     // per-warp hash slots: |L(b)| <= warp_max_deg <= 128
 constexpr uint32_t kFlushElems = 1u << 30;
 
@@ -103,8 +108,9 @@ __device__ __forceinline__ uint32_t find_req(uint32_t count, uint32_t i, F pre) 
 // Walk, for the pairs (b, c = N[b][j]), j in [j0, j1), 32 pairs per batch, the entries of N[c]
 // below b (rp = b's position in N[c], from the pair tables; pb + j indexes the pair) and count
 // each a found in the staged L(b).  MAP: L(b) is a direct map of two direction bits per id (every
-// a < b is in its range); else a hash.  One warp; the lanes share each batch's flattened (pair,
-// position) range.  Returns the entries walked (warp-uniform).
+// a < b is in its range); else a hash.  One warp: a batch's pairs with long prefixes are walked
+// one after another by all lanes, and the lanes share the flattened (pair, position) range of
+// the others.  Returns the entries walked (warp-uniform).
 template <bool OLD, bool MAP>
 __device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, const GraphDev& G, uint64_t bbase, uint64_t pb,
                                                uint32_t j0, uint32_t j1, const uint32_t* sH, const uint32_t* sO,
@@ -115,6 +121,34 @@ __device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, const GraphDe
     const uint32_t* __restrict__ rp = G.rp;
     const uint32_t le_mask = (2u << lane) - 1u;
     uint32_t walked = 0;
+    // one walked entry e_ca = a in N[c] of the pair whose b-c tricode bits are bcb (and whose c has
+    // the caller id oc2): look a up in L(b), count the triangle's tricode (or state) if found
+    auto count = [&](uint32_t e_ca, uint32_t bcb, uint32_t oc2) {
+        if (!e_ca) return;
+        const uint32_t a = e_ca >> 2;
+        uint32_t dir, oa = 0;
+        if (MAP) {   // word a / 16, bits 2 (a mod 16), read straight from the entry
+            dir = (sH[e_ca >> 6] >> ((e_ca >> 1) & 30u)) & 3u;
+            if (OLD && dir) oa = P.old[a];
+        } else {
+            uint32_t h = tri_hash(a, hb);
+            uint32_t e = sH[h];
+            while (e != 0u && (e >> 2) != a) {
+                h = (h + 1u) & hmask;
+                e = sH[h];
+            }
+            dir = e & 3u;
+            if (OLD && e) oa = sO[h];
+        }
+        if (dir != 0u) {
+            uint32_t t = tri_code(dir, bcb, e_ca);
+            if (OLD) {
+                const uint32_t ra = (oa > ob) + (oa > oc2), rb = (ob > oa) + (ob > oc2);
+                t = sPerm[(3u * ra + rb) * 64u + t];
+            }
+            atomicAdd(&myHist[t], 1u);
+        }
+    };
     for (uint32_t jb = j0; jb < j1; jb += 32) {
         const uint32_t j = jb + lane;
         const bool ok = j < j1;
@@ -123,6 +157,29 @@ __device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, const GraphDe
         uint64_t cb = ok ? off[c] : 0ull;
         uint32_t len = ok ? rp[pb + j] : 0u;
         uint32_t oc = (OLD && ok) ? P.old[c] : 0u;
+        if (kLongPrefix) {
+            // pairs with long prefixes, one at a time over the whole warp: consecutive entries,
+            // no search for the pair that holds an entry
+            uint32_t lm = __ballot_sync(0xffffffffu, len >= kLongPrefix);
+            while (lm) {
+                const int q = __ffs(lm) - 1;
+                lm &= lm - 1u;
+                const uint64_t B = __shfl_sync(0xffffffffu, cb, q);
+                const uint32_t L = __shfl_sync(0xffffffffu, len, q);
+                const uint32_t bcb = (__shfl_sync(0xffffffffu, e_bc, q) & 3u) << 2;
+                const uint32_t oq = OLD ? __shfl_sync(0xffffffffu, oc, q) : 0u;
+                walked += L;
+                for (uint32_t i = lane; i < L; i += 32u * kLongRounds) {
+                    uint32_t x[kLongRounds];
+#pragma unroll
+                    for (int r = 0; r < kLongRounds; ++r)
+                        x[r] = i + 32u * r < L ? __ldg(adj + (B + i + 32u * r)) : 0u;
+#pragma unroll
+                    for (int r = 0; r < kLongRounds; ++r) count(x[r], bcb, oq);
+                }
+            }
+            if (len >= kLongPrefix) len = 0u;
+        }
         // compact the pairs with a non-empty L(c) into lanes 0 .. cnt-1
         const uint32_t nz = __ballot_sync(0xffffffffu, len != 0u);
         if (!nz) continue;
@@ -171,35 +228,8 @@ __device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, const GraphDe
             const uint32_t iA = base + lane, iB = base + 32u + lane;
             const uint32_t xA = iA < total ? __ldg(adj + (BA + iA)) : 0u;
             const uint32_t xB = iB < total ? __ldg(adj + (BB + iB)) : 0u;
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const uint32_t e_ca = r ? xB : xA;
-                if (!e_ca) continue;
-                const uint32_t a = e_ca >> 2;
-                uint32_t dir, oa = 0;
-                if (MAP) {   // word a / 16, bits 2 (a mod 16), read straight from the entry
-                    dir = (sH[e_ca >> 6] >> ((e_ca >> 1) & 30u)) & 3u;
-                    if (OLD && dir) oa = P.old[a];
-                } else {
-                    uint32_t h = tri_hash(a, hb);
-                    uint32_t e = sH[h];
-                    while (e != 0u && (e >> 2) != a) {
-                        h = (h + 1u) & hmask;
-                        e = sH[h];
-                    }
-                    dir = e & 3u;
-                    if (OLD && e) oa = sO[h];
-                }
-                if (dir != 0u) {
-                    uint32_t t = tri_code(dir, r ? EB : EA, e_ca);
-                    if (OLD) {
-                        const uint32_t oc2 = r ? OB : OA;
-                        const uint32_t ra = (oa > ob) + (oa > oc2), rb = (ob > oa) + (ob > oc2);
-                        t = sPerm[(3u * ra + rb) * 64u + t];
-                    }
-                    atomicAdd(&myHist[t], 1u);
-                }
-            }
+            count(xA, EA, OA);
+            count(xB, EB, OB);
         }
     }
     return walked;
