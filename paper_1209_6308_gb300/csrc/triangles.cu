@@ -38,8 +38,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-// Prefixes of at least kLongPrefix entries are walked one pair at a time by the whole warp,
-// kLongRounds loads of 32 entries in flight per lane; shorter ones share flattened ranges.
+// Prefixes of at least kLongPrefix entries are walked one pair at a time by the whole warp
+// (walk_pairs<..., LONGW = true>), kLongRounds loads of 32 entries in flight per lane; shorter
+// ones share flattened ranges.
 // (Swept at scales 20 and 26: thresholds 64-512, 2-8 rounds.)
 constexpr uint32_t kLongPrefix = 128;
 constexpr int kLongRounds = 8;
@@ -111,7 +112,7 @@ __device__ __forceinline__ uint32_t find_req(uint32_t count, uint32_t i, F pre) 
 // a < b is in its range); else a hash.  One warp: a batch's pairs with long prefixes are walked
 // one after another by all lanes, and the lanes share the flattened (pair, position) range of
 // the others.  Returns the entries walked (warp-uniform).
-template <bool OLD, bool MAP>
+template <bool OLD, bool MAP, bool LONGW>
 __device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, const GraphDev& G, uint64_t bbase, uint64_t pb,
                                                uint32_t j0, uint32_t j1, const uint32_t* sH, const uint32_t* sO,
                                                int hb, uint32_t hmask, uint32_t ob, const uint8_t* sPerm,
@@ -157,7 +158,7 @@ __device__ __forceinline__ uint32_t walk_pairs(const TriParams& P, const GraphDe
         uint64_t cb = ok ? off[c] : 0ull;
         uint32_t len = ok ? rp[pb + j] : 0u;
         uint32_t oc = (OLD && ok) ? P.old[c] : 0u;
-        if (kLongPrefix) {
+        if (LONGW) {
             // pairs with long prefixes, one at a time over the whole warp: consecutive entries,
             // no search for the pair that holds an entry
             uint32_t lm = __ballot_sync(0xffffffffu, len >= kLongPrefix);
@@ -274,6 +275,10 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
     __shared__ uint32_t s_item, s_next;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the whole-warp walk of long prefixes, except in a batch of graphs (small graphs, short
+    // prefixes: the path would only cost the kernel registers); the one-warp tier's prefixes
+    // are below its degree bound, never long
+    constexpr bool kLongWalk = MODE != kTriBatch;
     if (P.phase && tid == 0) P.phase[3 * blockIdx.x] = tri_clock_ns();
     for (int k = tid; k < kWarps * 64; k += kThreads) sHist[k] = 0u;
     if (OLD)
@@ -334,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
                 uint32_t jb, g;
                 grab_pairs(&s_next, w.j1, lane, jb, g);
                 if (jb >= w.j1) break;
-                since_flush += walk_pairs<OLD, true>(P, G, bbase, pb, jb, min(jb + g, w.j1), sH, nullptr, 0, 0u, ob,
+                since_flush += walk_pairs<OLD, true, kLongWalk>(P, G, bbase, pb, jb, min(jb + g, w.j1), sH, nullptr, 0, 0u, ob,
                                                      sPerm, myHist, lane);
                 if (since_flush >= kFlushElems) {
                     flush_warp_hist(myHist, ghist, lane);
@@ -363,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
                 uint32_t jb, g;
                 grab_pairs(&s_next, w.j1, lane, jb, g);
                 if (jb >= w.j1) break;
-                since_flush += walk_pairs<OLD, false>(P, G, bbase, pb, jb, min(jb + g, w.j1), sH, sO, hb, hmask, ob,
+                since_flush += walk_pairs<OLD, false, kLongWalk>(P, G, bbase, pb, jb, min(jb + g, w.j1), sH, sO, hb, hmask, ob,
                                                       sPerm, myHist, lane);
                 if (since_flush >= kFlushElems) {
                     flush_warp_hist(myHist, ghist, lane);
@@ -427,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_triangles(TriParams P) {
                 if (OLD) wO[h] = P.old[e >> 2];
             }
             __syncwarp();
-            since_flush += walk_pairs<OLD, false>(P, G, bbase, G.ub[b] - lb, lb, db, wH, wO, hb, hmask,
+            since_flush += walk_pairs<OLD, false, false>(P, G, bbase, G.ub[b] - lb, lb, db, wH, wO, hb, hmask,
                                                   OLD ? P.old[b] : 0u, sPerm, myHist, lane);
             if (since_flush >= kFlushElems) {
                 flush_warp_hist(myHist, ghist, lane);
